@@ -1,0 +1,422 @@
+"""Benchmark: tagged uniform-BLR compressions per second on one GB300 (or N, weak scaling).
+
+One step = one full reconstruct_tag (Table 1) of the workload through the C ABI:
+tessellation, near-field offsets, test matrices, sketch, tag decode, combine,
+col (U and V), coupling and near field.  Inputs (points, T, G, H) are resident
+in HBM before timing; L2 is flushed (a 256 MiB write) before every step.
+
+Also reported:
+  e2e          the same metric through tblr_compress_host (host buffers,
+               host<->device copies inside the timed region);
+  roofline     the sketch kernel (the dominant one) timed with CUDA events on
+               its stream inside the timed steps, against the FP64 pipe peak;
+  cpu_baseline the CPU oracle timed on this host on a bounded sample of the
+               same workload, also used to check the GPU result's accuracy;
+  clocks       nvidia-smi samples taken during the timed region.
+
+``--impl reference`` times the CPU oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tagged-BLR compressions/s at rel.err≤1e-6 vs FP64; p50/p99 latency; % roofline"
+UNIT = "compressions/s"
+FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+WORKLOADS = {
+    # 2D Laplace, N = 65,536 i.i.d. uniform points, 16 x 16 boxes (~256 per box), k = 32, FP64
+    "laplace2d_n65536": dict(d=2, n=65536, grid=(16, 16), k=32, p=10, e=3, kernel="laplace2d",
+                             seed=0x7A660002),
+    # same recipe, 16,384 points on 8 x 8 boxes: the small case used for ncu captures
+    "laplace2d_n16384": dict(d=2, n=16384, grid=(8, 8), k=32, p=10, e=3, kernel="laplace2d",
+                             seed=0x7A660012),
+}
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def make_inputs(w, rank=0):
+    from paper_2501_05528_gb300 import inputs
+    d = w["d"]
+    pts = inputs.uniform_points(w["n"], d, seed=w["seed"] + 7919 * rank)
+    b = int(np.prod(w["grid"]))
+    ell = 3 ** d + 1 + w["e"]
+    T, G, H = inputs.tagging_draws(b, ell, w["n"], w["k"] + w["p"], seed=w["seed"] + 1 + 7919 * rank)
+    return pts, T, G, H
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(w, pts, T, G, H, boxes):
+    """The CPU oracle on a bounded sample: sketch rows, combine and col for `boxes`,
+    and the coupling blocks among them.  Returns (seconds, fraction of one
+    compression the sample stands for, per-box results)."""
+    from oracle import tagging as orc
+    t0 = time.perf_counter()
+    d = w["d"]
+    tess = orc.tessellate(pts, w["grid"], (0.0,) * d, (1.0,) * d)
+    op = orc.make_operator(w["kernel"], pts, tess)
+    r = w["k"] + w["p"]
+    Om = orc.extended_test_matrix(T, G, tess)
+    Ps = orc.extended_test_matrix(T, H, tess)
+    z, tau, rho = orc.decode(T, tess)
+    off = tess["offsets"]
+    ks = orc.box_ranks(tess, w["k"])
+    U, V = {}, {}
+    for i in boxes:
+        rows = np.arange(off[i], off[i + 1])
+        Y = orc.sketch_rows(op, Om, rows)
+        Z = orc.sketch_rows(op, Ps, rows)
+        S = sum(z[i, j] * Y[:, j * r:(j + 1) * r] for j in range(T.shape[1]))
+        R = sum(z[i, j] * Z[:, j * r:(j + 1) * r] for j in range(T.shape[1]))
+        U[i] = orc.col(S, ks[i])
+        V[i] = orc.col(R, ks[i])
+    blocks = {}
+    for i in boxes:
+        for j in boxes:
+            Ri = np.arange(off[i], off[i + 1])
+            Cj = np.arange(off[j], off[j + 1])
+            At = U[i].T @ op.block(Ri, Cj) @ V[j]
+            blocks[(i, j)] = U[i] @ At @ V[j].T
+    secs = time.perf_counter() - t0
+    b = len(off) - 1
+    return secs, len(boxes) / b, dict(tess=tess, U=U, V=V, blocks=blocks, ranks=ks)
+
+
+def sample_boxes(grid, count):
+    b = int(np.prod(grid))
+    step = max(1, b // count)
+    return list(range(step // 2, b, step))[:count]
+
+
+def compare_sample(sample, gpu):
+    """Relative Frobenius difference of the sampled far-field reconstructed blocks
+    U_i Atilde_ij V_j^T, GPU against oracle.  (Near pairs are left out: there
+    only U Atilde V^T + B is determined, and the sample has no B.)"""
+    off = sample["tess"]["offsets"]
+    nbrs = sample["tess"]["nbrs"]
+    num = den = 0.0
+    for (i, j), ref in sample["blocks"].items():
+        if j in nbrs[i]:
+            continue
+        ki, kj = int(sample["ranks"][i]), int(sample["ranks"][j])
+        Ui = gpu["u"][off[i]:off[i + 1], :ki]
+        Vj = gpu["v"][off[j]:off[j + 1], :kj]
+        blk = Ui @ gpu["at"][i, j][:ki, :kj] @ Vj.T
+        num += np.sum((blk - ref) ** 2)
+        den += np.sum(ref ** 2)
+    return math.sqrt(num / den) if den > 0 else float("nan")
+
+
+# ------------------------------------------------------------------ GPU arm
+
+class Runner:
+    """Preallocated buffers and the step chain of one compression (C-ABI calls)."""
+
+    def __init__(self, tb, torch, w, pts, T, G, H):
+        self.tb, self.torch = tb, torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t = lambda a: torch.as_tensor(a, device=dev)
+        self.pts, self.T, self.G, self.H = t(pts), t(T), t(G), t(H)
+        d = w["d"]
+        self.prob = tb.make_problem(d, w["kernel"], w["n"], w["grid"], (0.0,) * d, (1.0,) * d,
+                                    w["k"], w["p"], w["e"], precision=w.get("precision", 0))
+        self.sz = tb.tblr_sizes_of(self.prob)
+        lay = tb.tblr_tessellate(self.prob, self.pts)
+        nf_off, m_max = tb.tblr_nearfield_offsets(self.prob, lay)
+        torch.cuda.synchronize()
+        self.m_max = int(m_max.item())
+        self.total = int(nf_off[-1].item())
+        self.out = tb.tblr_compress(self.prob, lay, self.T, self.G, self.H,
+                                    nf=(nf_off, self.m_max, self.total))
+        self.lay = lay
+        n, sz = w["n"], self.sz
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.omega = torch.empty(sz.sketch_cols * n, **f64)
+        self.S = torch.empty(n, sz.r, **f64)
+        self.R = torch.empty(n, sz.r, **f64)
+        self.tws = torch.empty(tb.lib().tblr_tessellate_workspace(tb.ctypes.byref(self.prob)),
+                               dtype=torch.uint8, device=dev)
+        self.colws = torch.empty(tb.lib().tblr_col_workspace(tb.ctypes.byref(self.prob)),
+                                 dtype=torch.uint8, device=dev)
+        self.skws = torch.empty(max(1, tb.lib().tblr_sketch_workspace(tb.ctypes.byref(self.prob))),
+                                dtype=torch.uint8, device=dev)
+        self.nfws = torch.empty(tb.lib().tblr_nearfield_workspace(tb.ctypes.byref(self.prob),
+                                                                  self.m_max),
+                                dtype=torch.uint8, device=dev)
+        self.mmax_dev = torch.empty(1, dtype=torch.int32, device=dev)
+        self.host_total = torch.empty(1, dtype=torch.int64).pin_memory()
+        self.host_mmax = torch.empty(1, dtype=torch.int32).pin_memory()
+        self.launches_per_step = 15
+
+    def step(self, ev=None):
+        tb, L, P, o = self.tb, self.tb.lib(), self.tb.ctypes.byref(self.prob), self.out
+        p, s = self.tb._p, self.tb._stream()
+        ck = self.tb._check
+        lay = self.lay
+        ck(L.tblr_tessellate(P, p(self.pts), lay.ref, p(self.tws), self.tws.numel(), s), "tess")
+        ck(L.tblr_nearfield_offsets(P, lay.ref, p(o.nf_off), p(self.mmax_dev), s), "nf_off")
+        # sizes of this step's near-field output, read back as a user would
+        self.host_total.copy_(o.nf_off[-1:], non_blocking=True)
+        self.host_mmax.copy_(self.mmax_dev, non_blocking=True)
+        self.torch.cuda.current_stream().synchronize()
+        total, m_max = int(self.host_total[0]), int(self.host_mmax[0])
+        assert total == self.total and m_max == self.m_max
+        ck(L.tblr_test_matrices(P, lay.ref, p(self.T), p(self.G), p(self.H), p(self.omega), s), "tm")
+        if ev is not None:
+            ev[0].record()
+        ck(L.tblr_sketch(P, lay.ref, None, p(self.omega), p(o.yz), p(self.skws), self.skws.numel(),
+                         s), "sketch")
+        if ev is not None:
+            ev[1].record()
+        ck(L.tblr_decode(P, lay.ref, p(self.T), p(o.z), p(o.tau), p(o.rho), s), "decode")
+        ck(L.tblr_combine(P, lay.ref, p(o.yz), p(o.z), p(self.S), p(self.R), s), "combine")
+        ck(L.tblr_col(P, lay.ref, p(self.S), p(o.u), p(o.ranks), p(self.colws), self.colws.numel(),
+                      s), "col U")
+        ck(L.tblr_col(P, lay.ref, p(self.R), p(o.v), p(o.ranks), p(self.colws), self.colws.numel(),
+                      s), "col V")
+        ck(L.tblr_coupling(P, lay.ref, None, p(o.u), p(o.v), p(o.ranks), p(o.at), s), "coupling")
+        ck(L.tblr_nearfield(P, lay.ref, None, p(o.u), p(o.at), p(o.v), p(o.ranks), p(o.nf_off),
+                            m_max, p(o.bnear), p(self.nfws), self.nfws.numel(), s), "nearfield")
+
+
+def run_gpu(args, w):
+    import torch
+    import torch.distributed as dist
+    from paper_2501_05528_gb300 import tblr as tb
+
+    rank, local, world = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://", rank=rank, world_size=world,
+                                device_id=torch.device("cuda", local))
+    tb.lib()
+    pts, T, G, H = make_inputs(w, rank)
+    run = Runner(tb, torch, w, pts, T, G, H)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        run.step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    stp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    with sampler:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for i in range(args.steps):
+            flush.fill_(1)
+            stp[i][0].record()
+            run.step(evs[i])
+            stp[i][1].record()
+        t1.record()
+        barrier()
+    total_ms = t0.elapsed_time(t1)
+    step_ms = [a.elapsed_time(b) for a, b in stp]
+    sketch_ms = [a.elapsed_time(b) for a, b in evs]
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    value = args.steps * world / (total_ms / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    hp, hT, hG, hH = pin(pts), pin(T), pin(G), pin(H)
+    sz = run.sz
+    n, b, k, s3 = w["n"], sz.b, w["k"], sz.s3
+    outs = dict(perm=torch.empty(n, dtype=torch.int32).pin_memory(),
+                offsets=torch.empty(b + 1, dtype=torch.int32).pin_memory(),
+                nbr=torch.empty(b * s3, dtype=torch.int32).pin_memory(),
+                ranks=torch.empty(b, dtype=torch.int32).pin_memory(),
+                u=torch.empty(n, k, dtype=torch.float64).pin_memory(),
+                v=torch.empty(n, k, dtype=torch.float64).pin_memory(),
+                at=torch.empty(b, b, k, k, dtype=torch.float64).pin_memory(),
+                bnear=torch.empty(run.total, dtype=torch.float64).pin_memory())
+    tb.tblr_compress_host(run.prob, hp, hT, hG, hH, outputs=outs)   # warm-up (sizes the cache)
+    h2d = sum(x.numel() * x.element_size() for x in (hp, hT, hG, hH))
+    d2h = sum(outs[kk].numel() * outs[kk].element_size() for kk in outs if kk != "bnear_size")
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        tb.tblr_compress_host(run.prob, hp, hT, hG, hH, outputs=outs)
+    barrier()
+    te = time.perf_counter() - te
+    temax = torch.tensor([te], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(temax, op=dist.ReduceOp.MAX)
+    e2e_value = e2e_steps * world / float(temax.item())
+
+    result = None
+    if rank == 0:
+        flops = 2.0 * w["n"] * w["n"] * sz.sketch_cols
+        sk = statistics.mean(sketch_ms) / 1e3
+        achieved = flops / sk / 1e12
+        gpu_res = dict(u=run.out.u.cpu().numpy(), v=run.out.v.cpu().numpy(),
+                       at=run.out.at.cpu().numpy())
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            boxes = sample_boxes(w["grid"], args.cpu_sample_boxes)
+            secs, frac, sample = oracle_sample(w, pts, T, G, H, boxes)
+            relerr = compare_sample(sample, gpu_res)
+            cpu = {"value": frac / secs, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
+                   "kind": "oracle",
+                   "sample": (f"oracle sketch rows, combine and col for {len(boxes)} of "
+                              f"{sz.b} boxes plus their {len(boxes)**2} coupling blocks, "
+                              f"{secs:.1f} s, scaled by boxes/{len(boxes)}; numpy BLAS threads "
+                              f"on all cores, elementwise ops on one"),
+                   "gpu_relerr_vs_oracle_sampled": relerr}
+        lat = sorted(step_ms)
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if w.get("precision", 0) == 0 else "f16x3+f32acc/f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": w["n"], "d": w["d"],
+                       "grid": list(w["grid"]), "k": w["k"], "p": w["p"], "e": w["e"],
+                       "ell": sz.ell, "sketch_cols": sz.sketch_cols, "kernel": w["kernel"],
+                       "precision": "fp64" if w.get("precision", 0) == 0 else "mixed",
+                       "l2": "flushed by a 256 MiB write before every step",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": run.launches_per_step * args.steps,
+            "roofline": {"bound": "alu", "kernel": "apply_fp64_kernel (sketch)",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
+                         "sketch_ms": statistics.mean(sketch_ms)},
+            "cpu_baseline": cpu,
+            "clocks": sampler.summary(),
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def run_reference(args, w):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return None
+    pts, T, G, H = make_inputs(w, 0)
+    boxes = sample_boxes(w["grid"], args.cpu_sample_boxes)
+    for _ in range(args.warmup):
+        oracle_sample(w, pts, T, G, H, boxes)
+    times = []
+    frac = None
+    for _ in range(args.steps):
+        secs, frac, _ = oracle_sample(w, pts, T, G, H, boxes)
+        times.append(secs)
+    value = frac / statistics.mean(times)
+    cores = len(os.sched_getaffinity(0))
+    sample = (f"oracle sketch rows, combine and col for {len(boxes)} boxes and their coupling "
+              f"blocks per step, scaled by boxes/{len(boxes)}")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": w["n"], "d": w["d"],
+                       "grid": list(w["grid"]), "k": w["k"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="laplace2d_n65536", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-sample-boxes", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per sketch launch from an ncu capture, if current")
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    res = run_reference(args, w) if args.impl == "reference" else run_gpu(args, w)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,394 @@
+// Batched per-box post-processing, all FP64:
+//   a4 tag decode   z_i in null(T(N_i,:)), tau_i = T z_i, rho_i   (§4.1, §5.1, §5.3)
+//   a5 combine      S_i = sum_j z_ij Y_j(I_i,:)                   (Algorithm 2; eq. projected_tags)
+//   a6 col          U_i = k_i dominant left singular vectors of S_i (§2.3, §2.4)
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace tblr {
+namespace {
+
+// ---------------------------------------------------------------- a4 decode
+// One warp per box; lane j holds component j of ell-vectors (ell <= 32).
+// The rows of T(N_i,:) are orthonormalised by modified Gram-Schmidt with one
+// reorthogonalisation pass, then w = 1/sqrt(ell) is projected onto the
+// orthogonal complement (the null space) twice and normalised.
+constexpr int kDecWarps = 4;
+constexpr int kMaxNbr = 27;
+
+__global__ void __launch_bounds__(32 * kDecWarps) decode_kernel(
+    const double *__restrict__ T, int b, int ell, int s3, const int32_t *__restrict__ nbr,
+    const int32_t *__restrict__ nnbr, double *__restrict__ z, double *__restrict__ tau,
+    double *__restrict__ rho) {
+  __shared__ double Q[kDecWarps][kMaxNbr][32];
+  __shared__ double zs[kDecWarps][32];
+  __shared__ int rows[kDecWarps][kMaxNbr];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * kDecWarps + warp;
+  if (i >= b) return;
+  const int nb = nnbr[i];
+  for (int a = 0; a < nb; ++a) {
+    const int row = nbr[(int64_t)i * s3 + a];
+    if (lane == 0) rows[warp][a] = row;
+    double v = lane < ell ? T[(int64_t)row * ell + lane] : 0.0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int c = 0; c < a; ++c) {
+        const double qc = Q[warp][c][lane];
+        v -= warp_sum(qc * v) * qc;
+      }
+    v /= sqrt(warp_sum(v * v));
+    Q[warp][a][lane] = v;
+    __syncwarp();
+  }
+  double zv = lane < ell ? 1.0 / sqrt((double)ell) : 0.0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int c = 0; c < nb; ++c) {
+      const double qc = Q[warp][c][lane];
+      zv -= warp_sum(qc * zv) * qc;
+    }
+  zv /= sqrt(warp_sum(zv * zv));
+  if (lane < ell) z[(int64_t)i * ell + lane] = zv;
+  zs[warp][lane] = zv;
+  __syncwarp();
+  double amax = 0.0, amin = INFINITY;
+  bool anyfar = false;
+  for (int q = lane; q < b; q += 32) {
+    double t = 0.0;
+    for (int j = 0; j < ell; ++j) t = fma(T[(int64_t)q * ell + j], zs[warp][j], t);
+    tau[(int64_t)i * b + q] = t;
+    bool near = false;
+    for (int a = 0; a < nb; ++a) near |= rows[warp][a] == q;
+    if (!near) {
+      amax = fmax(amax, fabs(t));
+      amin = fmin(amin, fabs(t));
+      anyfar = true;
+    }
+  }
+  amax = warp_max(amax);
+  amin = warp_min(amin);
+  anyfar = __any_sync(0xffffffffu, anyfar);
+  if (lane == 0) rho[i] = anyfar ? amax / amin : NAN;
+}
+
+// --------------------------------------------------------------- a5 combine
+__global__ void combine_kernel(const double *__restrict__ yz, const double *__restrict__ z,
+                               const int32_t *__restrict__ box_of, int64_t n, int r, int ell,
+                               int64_t C, double *__restrict__ s, double *__restrict__ rr) {
+  const int64_t total = n * r;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = idx / r;
+    const int q = (int)(idx % r);
+    const double *zi = z + (int64_t)box_of[p] * ell;
+    const double *row = yz + p * 2 * C;
+    double a = 0.0, c = 0.0;
+    for (int j = 0; j < ell; ++j) {
+      const double w = zi[j];
+      a = fma(w, row[j * r + q], a);
+      c = fma(w, row[C + j * r + q], c);
+    }
+    s[idx] = a;
+    rr[idx] = c;
+  }
+}
+
+// ------------------------------------------------------------------- a6 col
+constexpr int kColThreads = 256;
+constexpr int kRMax = 112;
+
+__device__ double block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kColThreads / 32; ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+// Round-robin (circle) schedule over qq (even) columns: in round rho, column
+// qq-1 meets rho and (rho + k, rho - k) mod (qq - 1) meet for k = 1 .. qq/2-1.
+__device__ __forceinline__ void jacobi_pair(int rho, int k, int qq, int *a, int *b) {
+  const int m = qq - 1;
+  if (k == 0) {
+    *a = rho;
+    *b = m;
+  } else {
+    *a = (rho + k) % m;
+    *b = (rho - k + m) % m;
+  }
+}
+
+struct ColArgs {
+  const double *S;
+  double *U;
+  int32_t *ranks;
+  double *W;  // workspace, column-major m_i x r per box at offset off_i * r
+  double *E;  // workspace, column-major m_i x k per box at offset off_i * k
+  const int32_t *offsets;
+  const int32_t *nnbr;
+  int r, k, b;
+};
+
+__global__ void __launch_bounds__(kColThreads) col_kernel(ColArgs A) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nw = kColThreads / 32;
+  const int i = blockIdx.x;
+  const int off = A.offsets[i], m = A.offsets[i + 1] - off;
+  const int r = A.r, k = A.k;
+  const int ki = (A.nnbr[i] < A.b) ? min(k, m) : 0;
+  if (tid == 0) A.ranks[i] = ki;
+  double *U = A.U + (int64_t)off * k;
+  if (ki == 0) {
+    for (int idx = tid; idx < m * k; idx += kColThreads) U[idx] = 0.0;
+    return;
+  }
+  const int q = min(m, r);
+  double *W = A.W + (int64_t)off * r;
+  double *E = A.E + (int64_t)off * k;
+  double *tauh = sm;             // [kRMax]
+  double *red = tauh + kRMax;    // [8]
+  double *B = red + 8;           // [q][r]: column a of R^T (= row a of R)
+  double *X = B + q * r;         // [q][q]: column-major rotations
+  double *sig = X + q * q;       // [q]
+  int *order = reinterpret_cast<int *>(sig + q);  // [q]
+  __shared__ int rotated;
+
+  // Working copy of S_i, column-major.
+  for (int idx = tid; idx < m * r; idx += kColThreads) {
+    const int p = idx / r, c = idx % r;
+    W[(int64_t)c * m + p] = A.S[((int64_t)off + p) * r + c];
+  }
+  __syncthreads();
+
+  // Householder QR (§2.2), reflector j: H_j = I - tau_j v v^T, v_j = 1,
+  // v below the diagonal stored in column j, beta on the diagonal.
+  for (int j = 0; j < q; ++j) {
+    double part = 0.0;
+    for (int p = j + 1 + tid; p < m; p += kColThreads) {
+      const double v = W[(int64_t)j * m + p];
+      part += v * v;
+    }
+    const double sigma = block_sum(part, red);
+    const double alpha = W[(int64_t)j * m + j];
+    double t = 0.0, beta = alpha, scale = 0.0;
+    if (sigma != 0.0) {
+      beta = -copysign(sqrt(alpha * alpha + sigma), alpha);
+      t = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    __syncthreads();
+    for (int p = j + 1 + tid; p < m; p += kColThreads) W[(int64_t)j * m + p] *= scale;
+    if (tid == 0) {
+      W[(int64_t)j * m + j] = beta;
+      tauh[j] = t;
+    }
+    __syncthreads();
+    if (t != 0.0) {
+      for (int c = j + 1 + warp; c < r; c += nw) {
+        double d = lane == 0 ? W[(int64_t)c * m + j] : 0.0;
+        for (int p = j + 1 + lane; p < m; p += 32) d += W[(int64_t)j * m + p] * W[(int64_t)c * m + p];
+        const double wv = warp_sum(d) * t;
+        if (lane == 0) W[(int64_t)c * m + j] -= wv;
+        for (int p = j + 1 + lane; p < m; p += 32) W[(int64_t)c * m + p] -= wv * W[(int64_t)j * m + p];
+      }
+    }
+    __syncthreads();
+  }
+
+  // B = R^T (r x q, column a = row a of R), X = I.
+  for (int idx = tid; idx < q * r; idx += kColThreads) {
+    const int a = idx / r, c = idx % r;
+    B[idx] = (c >= a) ? W[(int64_t)c * m + a] : 0.0;
+  }
+  for (int idx = tid; idx < q * q; idx += kColThreads) X[idx] = (idx / q == idx % q) ? 1.0 : 0.0;
+  if (tid == 0) rotated = 0;
+  __syncthreads();
+
+  // One-sided (Hestenes) Jacobi on the columns of R^T: R^T X = B with
+  // orthogonal columns, so R = X diag(|B_a|) (B_a/|B_a|)^T and the columns of
+  // X are R's left singular vectors.
+  const int qq = q + (q & 1);
+  const double tol = 1e-15;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int rho = 0; rho < qq - 1; ++rho) {
+      for (int pr = warp; pr < qq / 2; pr += nw) {
+        int a, bb;
+        jacobi_pair(rho, pr, qq, &a, &bb);
+        if (a >= q || bb >= q) continue;
+        if (a > bb) {
+          const int tt = a;
+          a = bb;
+          bb = tt;
+        }
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int c = lane; c < r; c += 32) {
+          const double x = B[a * r + c], y = B[bb * r + c];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double tn = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + tn * tn), sn = cs * tn;
+          for (int c = lane; c < r; c += 32) {
+            const double x = B[a * r + c], y = B[bb * r + c];
+            B[a * r + c] = cs * x - sn * y;
+            B[bb * r + c] = sn * x + cs * y;
+          }
+          for (int c = lane; c < q; c += 32) {
+            const double x = X[a * q + c], y = X[bb * q + c];
+            X[a * q + c] = cs * x - sn * y;
+            X[bb * q + c] = sn * x + cs * y;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+  }
+
+  // Singular values and their descending order (ties: lower index first).
+  for (int a = warp; a < q; a += nw) {
+    double s2 = 0.0;
+    for (int c = lane; c < r; c += 32) s2 += B[a * r + c] * B[a * r + c];
+    s2 = warp_sum(s2);
+    if (lane == 0) sig[a] = sqrt(s2);
+  }
+  __syncthreads();
+  for (int a = tid; a < q; a += kColThreads) {
+    int rank = 0;
+    for (int c = 0; c < q; ++c) rank += (sig[c] > sig[a]) || (sig[c] == sig[a] && c < a);
+    order[rank] = a;
+  }
+  __syncthreads();
+
+  // E = Q [X(:, order[0:ki]); 0], Q = H_0 H_1 ... H_{q-1}.
+  for (int idx = tid; idx < ki * m; idx += kColThreads) {
+    const int tcol = idx / m, p = idx % m;
+    E[(int64_t)tcol * m + p] = (p < q) ? X[order[tcol] * q + p] : 0.0;
+  }
+  __syncthreads();
+  for (int j = q - 1; j >= 0; --j) {
+    const double t = tauh[j];
+    if (t != 0.0) {
+      for (int tcol = warp; tcol < ki; tcol += nw) {
+        double *e = E + (int64_t)tcol * m;
+        double d = lane == 0 ? e[j] : 0.0;
+        for (int p = j + 1 + lane; p < m; p += 32) d += W[(int64_t)j * m + p] * e[p];
+        const double wv = warp_sum(d) * t;
+        if (lane == 0) e[j] -= wv;
+        for (int p = j + 1 + lane; p < m; p += 32) e[p] -= wv * W[(int64_t)j * m + p];
+      }
+    }
+    __syncthreads();
+  }
+
+  // Sign rule, then write U_i (zero columns beyond k_i).
+  for (int tcol = warp; tcol < k; tcol += nw) {
+    double sgn = 1.0;
+    if (tcol < ki) {
+      const double *e = E + (int64_t)tcol * m;
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      for (int p = lane; p < m; p += 32) {
+        const double v = fabs(e[p]);
+        if (v > best) {
+          best = v;
+          bi = p;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      sgn = (e[bi] < 0.0) ? -1.0 : 1.0;
+    }
+    for (int p = lane; p < m; p += 32)
+      U[(int64_t)p * k + tcol] = (tcol < ki) ? sgn * E[(int64_t)tcol * m + p] : 0.0;
+  }
+}
+
+size_t col_smem(int r) {
+  const int q = r;  // q <= r
+  return sizeof(double) * (kRMax + 8 + (size_t)q * r + (size_t)q * q + q) + sizeof(int) * q;
+}
+
+}  // namespace
+}  // namespace tblr
+
+using namespace tblr;
+
+extern "C" int tblr_decode(const tblr_problem *prob, const tblr_layout *lay, const double *T,
+                           double *z, double *tau, double *rho, void *stream) {
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_TRY(check_layout(P, lay));
+  TBLR_REQUIRE(T && z && tau && rho, "T, z, tau and rho must be non-NULL");
+  TBLR_REQUIRE(P.ell <= 32, "tag decode supports ell <= 32 (got %d)", P.ell);
+  decode_kernel<<<(unsigned)cdiv(P.b, kDecWarps), 32 * kDecWarps, 0, as_stream(stream)>>>(
+      T, (int)P.b, P.ell, P.s3, lay->nbr, lay->nnbr, z, tau, rho);
+  return launch_status("decode_kernel");
+}
+
+extern "C" int tblr_combine(const tblr_problem *prob, const tblr_layout *lay, const double *yz,
+                            const double *z, double *s, double *rr, void *stream) {
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_TRY(check_layout(P, lay));
+  TBLR_REQUIRE(yz && z && s && rr, "yz, z, s and rr must be non-NULL");
+  const int64_t total = P.n * P.r;
+  const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(total, 256), 152 * 16);
+  combine_kernel<<<blocks, 256, 0, as_stream(stream)>>>(yz, z, lay->box_of, P.n, P.r, P.ell, P.C,
+                                                        s, rr);
+  return launch_status("combine_kernel");
+}
+
+extern "C" size_t tblr_col_workspace(const tblr_problem *prob) {
+  Prob P;
+  if (check_problem(prob, &P) != TBLR_OK) return 0;
+  return align256(sizeof(double) * P.n * P.r) + align256(sizeof(double) * P.n * P.k);
+}
+
+extern "C" int tblr_col(const tblr_problem *prob, const tblr_layout *lay, const double *s,
+                        double *u, int32_t *ranks, void *ws, size_t ws_bytes, void *stream) {
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_TRY(check_layout(P, lay));
+  TBLR_REQUIRE(s && u && ranks, "s, u and ranks must be non-NULL");
+  TBLR_REQUIRE(P.r <= kRMax, "col supports r <= %d (got %d)", kRMax, P.r);
+  TBLR_REQUIRE(ws != nullptr && ws_bytes >= tblr_col_workspace(prob), "col workspace too small");
+  ColArgs A;
+  A.S = s;
+  A.U = u;
+  A.ranks = ranks;
+  A.W = static_cast<double *>(ws);
+  A.E = reinterpret_cast<double *>(static_cast<char *>(ws) + align256(sizeof(double) * P.n * P.r));
+  A.offsets = lay->offsets;
+  A.nnbr = lay->nnbr;
+  A.r = P.r;
+  A.k = P.k;
+  A.b = (int)P.b;
+  const size_t smem = col_smem(P.r);
+  TBLR_CUDA(cudaFuncSetAttribute(col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  col_kernel<<<(unsigned)P.b, kColThreads, smem, as_stream(stream)>>>(A);
+  return launch_status("col_kernel");
+}

@@ -1,0 +1,227 @@
+// a2 (extended test matrices, §4.1 eq. extend_test_mat), the FP64 black-box
+// apply Y = A X with A generated tile by tile, and a3 (sketch, Algorithm 2).
+//
+// FP64 apply design (GB300 runs DFMA at ~1.2 TFLOP/s, so the kernel is bound
+// by the FP64 pipe, not by memory): a CTA owns BM = 16 rows of Y and up to
+// 256 * CPT columns; each step generates the BM x BK tile of A once (one entry
+// per thread; a log or rsqrt costs ~36 DFMA) and contracts it with the
+// BK x (256 CPT) slice of X staged in shared memory, so every generated entry
+// feeds up to 1280 DFMAs.
+#include "common.cuh"
+#include "mixed.cuh"
+
+namespace tblr {
+namespace {
+
+constexpr int kTM = 32;  // points per test-matrix tile
+
+// Omega(I_i, j r + q) = T[i, j] G_i(:, q); side 0 writes Omega from G, side 1
+// writes Psi from H.  Output K-major: out[(side*C + j r + q) * n + p].
+__global__ void __launch_bounds__(256) test_matrices_kernel(
+    const double *__restrict__ T, const double *__restrict__ G, const double *__restrict__ H,
+    const int32_t *__restrict__ perm, const int32_t *__restrict__ box_of, int64_t n, int r,
+    int ell, double *__restrict__ out) {
+  extern __shared__ double sm[];
+  double *tile = sm;                     // [kTM][r + 1]
+  double *tb = sm + kTM * (r + 1);       // [kTM][ell]
+  const int side = blockIdx.y;
+  const double *src = side ? H : G;
+  const int64_t p0 = (int64_t)blockIdx.x * kTM;
+  for (int idx = threadIdx.x; idx < kTM * r; idx += blockDim.x) {
+    const int pl = idx / r, q = idx % r;
+    const int64_t p = p0 + pl;
+    tile[pl * (r + 1) + q] = (p < n) ? src[(int64_t)perm[p] * r + q] : 0.0;
+  }
+  for (int idx = threadIdx.x; idx < kTM * ell; idx += blockDim.x) {
+    const int pl = idx / ell, j = idx % ell;
+    const int64_t p = p0 + pl;
+    tb[pl * ell + j] = (p < n) ? T[(int64_t)box_of[p] * ell + j] : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t C = (int64_t)ell * r;
+  const int64_t p = p0 + lane;
+  for (int64_t c = warp; c < C; c += nw) {
+    const int j = (int)(c / r), q = (int)(c % r);
+    if (p < n) out[(side * C + c) * n + p] = tb[lane * ell + j] * tile[lane * (r + 1) + q];
+  }
+}
+
+constexpr int kBM = 16, kBK = 16, kThreads = 256;
+
+template <class Op, int CPT>
+__global__ void __launch_bounds__(kThreads, 1)
+    apply_fp64_kernel(Op op, const double *__restrict__ xt, int64_t n, int64_t ncols,
+                      double *__restrict__ y, int64_t ldy) {
+  extern __shared__ double sm[];
+  constexpr int NT = kThreads * CPT;
+  double *As = sm;               // [kBK][kBM]
+  double *Xs = sm + kBK * kBM;   // [kBK][NT]
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * kBM;
+  const int64_t col0 = (int64_t)blockIdx.y * NT;
+  bool active[CPT];
+#pragma unroll
+  for (int s = 0; s < CPT; ++s) active[s] = col0 + kThreads * s + warp * 32 < ncols;
+
+  double acc[kBM][CPT];
+#pragma unroll
+  for (int r = 0; r < kBM; ++r)
+#pragma unroll
+    for (int s = 0; s < CPT; ++s) acc[r][s] = 0.0;
+
+  for (int64_t k0 = 0; k0 < n; k0 += kBK) {
+    __syncthreads();
+    {
+      const int r = tid % kBM, kk = tid / kBM;  // kBM * kBK == kThreads
+      const int64_t gi = row0 + r, gj = k0 + kk;
+      double v = 0.0;
+      if (gi < n && gj < n) v = op(gi, gj);
+      As[kk * kBM + r] = v;
+    }
+#pragma unroll
+    for (int s = 0; s < CPT; ++s) {
+      const int cl = tid + kThreads * s;
+      const int64_t c = col0 + cl;
+#pragma unroll
+      for (int kk = 0; kk < kBK; ++kk) {
+        double v = 0.0;
+        if (c < ncols && k0 + kk < n) v = __ldg(xt + c * n + k0 + kk);
+        Xs[kk * NT + cl] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kBK; ++kk) {
+      double a[kBM];
+#pragma unroll
+      for (int r = 0; r < kBM; r += 2) {
+        const double2 t = *reinterpret_cast<const double2 *>(As + kk * kBM + r);
+        a[r] = t.x;
+        a[r + 1] = t.y;
+      }
+#pragma unroll
+      for (int s = 0; s < CPT; ++s) {
+        if (active[s]) {
+          const double x = Xs[kk * NT + tid + kThreads * s];
+#pragma unroll
+          for (int r = 0; r < kBM; ++r) acc[r][s] = fma(a[r], x, acc[r][s]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < CPT; ++s) {
+    const int64_t c = col0 + tid + kThreads * s;
+    if (c >= ncols) continue;
+#pragma unroll
+    for (int r = 0; r < kBM; ++r) {
+      const int64_t gi = row0 + r;
+      if (gi < n) y[gi * ldy + c] = acc[r][s];
+    }
+  }
+}
+
+template <class Op, int CPT>
+int launch_apply_fp64_cpt(const Op &op, const double *xt, int64_t n, int64_t ncols, double *y,
+                          int64_t ldy, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (kBK * kBM + kBK * kThreads * CPT);
+  auto kern = apply_fp64_kernel<Op, CPT>;
+  TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)cdiv(n, kBM), (unsigned)cdiv(ncols, kThreads * CPT));
+  kern<<<grid, kThreads, smem, s>>>(op, xt, n, ncols, y, ldy);
+  return launch_status("apply_fp64_kernel");
+}
+
+template <class Op>
+int launch_apply_fp64(const Op &op, const double *xt, int64_t n, int64_t ncols, double *y,
+                      int64_t ldy, cudaStream_t s) {
+  const int64_t cpt = cdiv(ncols, kThreads);
+  if (cpt <= 1) return launch_apply_fp64_cpt<Op, 1>(op, xt, n, ncols, y, ldy, s);
+  if (cpt <= 2) return launch_apply_fp64_cpt<Op, 2>(op, xt, n, ncols, y, ldy, s);
+  if (cpt <= 3) return launch_apply_fp64_cpt<Op, 3>(op, xt, n, ncols, y, ldy, s);
+  if (cpt <= 4) return launch_apply_fp64_cpt<Op, 4>(op, xt, n, ncols, y, ldy, s);
+  return launch_apply_fp64_cpt<Op, 5>(op, xt, n, ncols, y, ldy, s);
+}
+
+}  // namespace
+
+int apply_any(const Prob &P, const tblr_layout *lay, const double *dense, const double *xt,
+              int64_t ncols, double *y, int64_t ldy, int adjoint, int precision, void *ws,
+              size_t ws_bytes, cudaStream_t s) {
+  if (ncols == 0) return TBLR_OK;
+  if (precision == TBLR_MIXED) {
+    TBLR_REQUIRE(symmetric_kernel(P.kernel), "mixed precision needs a built-in kernel operator");
+    return apply_mixed(P, lay, xt, ncols, y, ldy, ws, ws_bytes, s);
+  }
+  return with_operator(P, lay, dense, adjoint, [&](auto op) {
+    return launch_apply_fp64(op, xt, P.n, ncols, y, ldy, s);
+  });
+}
+
+}  // namespace tblr
+
+using namespace tblr;
+
+extern "C" int tblr_test_matrices(const tblr_problem *prob, const tblr_layout *lay,
+                                  const double *T, const double *G, const double *H,
+                                  double *omega_psi, void *stream) {
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_TRY(check_layout(P, lay));
+  TBLR_REQUIRE(T && G && H && omega_psi, "T, G, H and omega_psi must be non-NULL");
+  TBLR_REQUIRE(P.r <= 512 && P.ell <= 128, "r <= 512 and ell <= 128 required");
+  const size_t smem = sizeof(double) * (kTM * (P.r + 1) + kTM * P.ell);
+  if (smem > 48 * 1024)
+    TBLR_CUDA(cudaFuncSetAttribute(test_matrices_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  dim3 grid((unsigned)cdiv(P.n, kTM), 2);
+  test_matrices_kernel<<<grid, 256, smem, as_stream(stream)>>>(T, G, H, lay->perm, lay->box_of, P.n,
+                                                               P.r, P.ell, omega_psi);
+  return launch_status("test_matrices_kernel");
+}
+
+extern "C" size_t tblr_apply_workspace(const tblr_problem *prob, int64_t ncols, int precision) {
+  Prob P;
+  if (check_problem(prob, &P) != TBLR_OK) return 0;
+  return precision == TBLR_MIXED ? mixed_workspace(P, ncols) : 0;
+}
+
+extern "C" int tblr_apply(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
+                          const double *xt, int64_t ncols, double *y, int64_t ldy, int adjoint,
+                          int precision, void *ws, size_t ws_bytes, void *stream) {
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_TRY(check_layout(P, lay));
+  TBLR_REQUIRE(xt && y, "xt and y must be non-NULL");
+  TBLR_REQUIRE(ncols >= 0 && ncols <= 8192 && ldy >= ncols, "need 0 <= ncols <= 8192, ldy >= ncols");
+  TBLR_REQUIRE(precision == TBLR_FP64 || precision == TBLR_MIXED, "bad precision");
+  return apply_any(P, lay, dense, xt, ncols, y, ldy, adjoint, precision, ws, ws_bytes,
+                   as_stream(stream));
+}
+
+extern "C" size_t tblr_sketch_workspace(const tblr_problem *prob) {
+  Prob P;
+  if (check_problem(prob, &P) != TBLR_OK) return 0;
+  return P.precision == TBLR_MIXED ? mixed_workspace(P, 2 * P.C) : 0;
+}
+
+extern "C" int tblr_sketch(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
+                           const double *omega_psi, double *yz, void *ws, size_t ws_bytes,
+                           void *stream) {
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_TRY(check_layout(P, lay));
+  TBLR_REQUIRE(omega_psi && yz, "omega_psi and yz must be non-NULL");
+  TBLR_REQUIRE(2 * P.C <= 8192, "2 ell r must be <= 8192");
+  cudaStream_t s = as_stream(stream);
+  const int64_t C = P.C;
+  if (symmetric_kernel(P.kernel)) {
+    // A^T = A: Y and Z come from one pass over A with [Omega | Psi].
+    return apply_any(P, lay, dense, omega_psi, 2 * C, yz, 2 * C, 0, P.precision, ws, ws_bytes, s);
+  }
+  TBLR_REQUIRE(P.precision == TBLR_FP64, "mixed precision needs a built-in kernel operator");
+  TBLR_TRY(apply_any(P, lay, dense, omega_psi, C, yz, 2 * C, 0, TBLR_FP64, ws, ws_bytes, s));
+  return apply_any(P, lay, dense, omega_psi + C * P.n, C, yz + C, 2 * C, 1, TBLR_FP64, ws, ws_bytes,
+                   s);
+}

@@ -1,0 +1,212 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, on the same seeded inputs.
+
+Cases are sized so the oracle finishes in seconds while spanning several tiles
+with ragged tails (n not a multiple of the 16-row tile, sketch columns not a
+multiple of 256), plus the degenerate geometries: empty boxes, boxes with fewer
+points than k, a grid without far field, and d = 1.
+
+Tolerances (FP64 path): index lists and the test matrices bit-exact; sketch
+and per-step floating outputs within 1e-11 relative (they differ only by
+summation order and 1-ulp differences of log/rsqrt); the reconstruction
+A_uBLR within 1e-10 relative Frobenius (the FP64 parity bound).  The exactly
+uniform BLR case must also reproduce A itself to 1e-12.
+"""
+import numpy as np
+import pytest
+
+from oracle import tagging as orc
+from paper_2501_05528_gb300 import inputs
+from tests import metrics
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _tb():
+    from paper_2501_05528_gb300 import tblr
+    return tblr
+
+
+CASES = {
+    "exact_ublr_2d": dict(kind="dense", d=2, grid=(4, 4), k=8, e=3, seed=1),
+    "laplace2d_ragged": dict(kind="laplace2d", d=2, grid=(6, 6), n=3001, k=8, e=3, seed=2),
+    "laplace3d_ragged": dict(kind="laplace3d", d=3, grid=(4, 4, 4), n=2501, k=6, e=1, seed=3),
+    "dense_1d_small_boxes": dict(kind="dense1d", d=1, grid=(9,), n=70, k=16, e=0, seed=4),
+    "laplace2d_empty_boxes": dict(kind="laplace2d_holes", d=2, grid=(5, 5), n=900, k=6, e=2, seed=5),
+    "laplace2d_no_farfield": dict(kind="laplace2d", d=2, grid=(2, 2), n=300, k=5, e=3, seed=6),
+}
+
+
+def _make_inputs(c):
+    d, grid, seed = c["d"], c["grid"], c["seed"]
+    lo, hi = (0.0,) * d, (1.0,) * d
+    dense = None
+    if c["kind"] == "dense":
+        pts, owner = inputs.box_points(grid, 64, seed)
+        dense = inputs.exact_ublr_matrix(owner, c["k"], seed + 100)
+        kind = "dense"
+    elif c["kind"] == "dense1d":
+        pts = inputs.uniform_points(c["n"], 1, seed)
+        dense = np.random.default_rng(seed + 100).standard_normal((c["n"], c["n"]))
+        kind = "dense"
+    elif c["kind"] == "laplace2d_holes":
+        pts = inputs.uniform_points(c["n"], 2, seed)
+        keep = ~((pts[:, 0] > 0.4) & (pts[:, 0] < 0.8) & (pts[:, 1] > 0.2) & (pts[:, 1] < 0.6))
+        pts = pts[keep]
+        kind = "laplace2d"
+    else:
+        pts = inputs.uniform_points(c["n"], d, seed)
+        kind = c["kind"]
+    b = int(np.prod(grid))
+    ell = orc.tag_columns(d, c["e"])
+    r = c["k"] + 10
+    T, G, H = inputs.tagging_draws(b, ell, len(pts), r, seed + 200)
+    return dict(pts=pts, kind=kind, dense=dense, T=T, G=G, H=H, lo=lo, hi=hi, ell=ell, r=r)
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    tb = _tb()
+    c = CASES[request.param]
+    x = _make_inputs(c)
+    d, grid, k = c["d"], c["grid"], c["k"]
+    n = len(x["pts"])
+    res = orc.reconstruct_tag(x["pts"], grid, x["lo"], x["hi"], x["kind"], x["T"], x["G"], x["H"],
+                              k, 10, dense=x["dense"])
+    dev = torch.device("cuda")
+    prob = tb.make_problem(d, x["kind"], n, grid, x["lo"], x["hi"], k, 10, c["e"])
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    pts, T, G, H = t(x["pts"]), t(x["T"]), t(x["G"]), t(x["H"])
+    dense = None if x["dense"] is None else t(x["dense"])
+    lay = tb.tblr_tessellate(prob, pts)
+    nf_off, m_max = tb.tblr_nearfield_offsets(prob, lay)
+    om = tb.tblr_test_matrices(prob, lay, T, G, H)
+    yz = tb.tblr_sketch(prob, lay, om, dense=dense)
+    z, tau, rho = tb.tblr_decode(prob, lay, T)
+    s, rr = tb.tblr_combine(prob, lay, yz, z)
+    u, ranks = tb.tblr_col(prob, lay, s)
+    v, ranks_v = tb.tblr_col(prob, lay, rr)
+    at = tb.tblr_coupling(prob, lay, u, v, ranks, dense=dense)
+    mm, total = int(m_max.item()), int(nf_off[-1].item())
+    bn = tb.tblr_nearfield(prob, lay, u, at, v, ranks, nf_off, mm, total, dense=dense)
+    full = tb.tblr_compress(prob, lay, T, G, H, dense=dense)
+    torch.cuda.synchronize()
+    h = lambda a: a.cpu().numpy()
+    gpu = dict(perm=h(lay.perm), offsets=h(lay.offsets), nbr=h(lay.nbr), nnbr=h(lay.nnbr),
+               colour=h(lay.colour), pts=h(lay.pts).reshape(d, n).T, omega=h(om).reshape(-1, n).T,
+               yz=h(yz), z=h(z), tau=h(tau), rho=h(rho), s=h(s), rr=h(rr), u=h(u), v=h(v),
+               ranks=h(ranks), ranks_v=h(ranks_v), at=h(at), nf_off=h(nf_off), m_max=mm,
+               bnear=h(bn)[:total], full=full, prob=prob)
+    return dict(name=request.param, c=c, x=x, res=res, gpu=gpu, n=n)
+
+
+def test_tessellation_bit_exact(case):
+    g, res = case["gpu"], case["res"]
+    tess = res["tess"]
+    s3 = 3 ** case["c"]["d"]
+    assert np.array_equal(g["perm"], tess["perm"])
+    assert np.array_equal(g["offsets"], tess["offsets"])
+    nbr, cnt = metrics.padded_neighbours(tess["nbrs"], s3)
+    assert np.array_equal(g["nbr"], nbr)
+    assert np.array_equal(g["nnbr"], cnt)
+    assert np.array_equal(g["colour"], tess["colour"])
+    assert np.array_equal(g["pts"], case["x"]["pts"][tess["perm"]])
+    off = tess["offsets"]
+    assert g["m_max"] == int(np.max(np.diff(off)))
+
+
+def test_test_matrices_bit_exact(case):
+    g, res = case["gpu"], case["res"]
+    assert np.array_equal(g["omega"], np.hstack([res["Omega"], res["Psi"]]))
+
+
+def test_sketch_matches(case):
+    g, res = case["gpu"], case["res"]
+    ref = np.hstack([res["Y"], res["Z"]])
+    assert metrics.rel(g["yz"], ref) < 1e-12
+
+
+def test_decode_matches(case):
+    g, res = case["gpu"], case["res"]
+    assert np.abs(g["z"] - res["z"]).max() < 1e-13
+    assert np.abs(g["tau"] - res["tau"]).max() < 1e-12 * max(1.0, np.abs(res["tau"]).max())
+    assert np.array_equal(np.isnan(g["rho"]), np.isnan(res["rho"]))
+    ok = ~np.isnan(res["rho"])
+    assert np.allclose(g["rho"][ok], res["rho"][ok], rtol=1e-10, atol=0)
+
+
+def test_combine_matches(case):
+    g, res = case["gpu"], case["res"]
+    assert metrics.rel(g["s"], res["S"]) < 1e-11
+    assert metrics.rel(g["rr"], res["R"]) < 1e-11
+
+
+def test_ranks_and_bases(case):
+    g, res = case["gpu"], case["res"]
+    assert np.array_equal(g["ranks"], res["ranks"])
+    assert np.array_equal(g["ranks_v"], res["ranks"])
+    off = res["tess"]["offsets"]
+    for i in range(len(off) - 1):
+        ki = int(res["ranks"][i])
+        rows = slice(off[i], off[i + 1])
+        Ug, Uo = g["u"][rows, :ki], res["U"][rows, :ki]
+        if ki:
+            assert np.abs(Ug.T @ Ug - np.eye(ki)).max() < 1e-13
+            # range of the sample captured by each basis (basis-independent)
+            S = res["S"][rows]
+            Pg = Ug @ (Ug.T @ S)
+            Po = Uo @ (Uo.T @ S)
+            assert np.linalg.norm(Pg - Po) <= 1e-10 * np.linalg.norm(S)
+        assert np.all(g["u"][rows, ki:] == 0.0)
+
+
+def test_reconstruction_matches_oracle(case):
+    g, res = case["gpu"], case["res"]
+    tess = res["tess"]
+    s3 = 3 ** case["c"]["d"]
+    off = tess["offsets"]
+    nbr, cnt = metrics.padded_neighbours(tess["nbrs"], s3)
+    Bg = metrics.blocks_from_flat(g["bnear"], g["nf_off"], nbr, cnt, off, s3)
+    rep_g = dict(U=g["u"], V=g["v"], At=g["at"], B=Bg)
+    rep_o = dict(U=res["U"], V=res["V"], At=res["coupling"], B=res["nearfield"])
+    err = metrics.ublr_difference(off, nbr, cnt, s3, res["ranks"], rep_g, rep_o)
+    assert err <= 1e-10, err
+    for key in Bg:
+        ref = res["nearfield"][key]
+        if ref.size:
+            assert np.linalg.norm(Bg[key] - ref) <= 1e-10 * max(np.linalg.norm(ref), 1e-300) + 1e-12
+
+
+def test_whole_pipeline_equals_step_chain(case):
+    g = case["gpu"]
+    f = g["full"]
+    total = f.total
+    for name, ref in (("yz", g["yz"]), ("z", g["z"]), ("u", g["u"]), ("v", g["v"]), ("at", g["at"])):
+        assert np.array_equal(getattr(f, name).cpu().numpy(), ref), name
+    assert np.array_equal(f.bnear.cpu().numpy()[:total], g["bnear"])
+
+
+def test_exact_ublr_reproduces_a(case):
+    if case["name"] != "exact_ublr_2d":
+        pytest.skip("exactly uniform BLR input only")
+    g, res = case["gpu"], case["res"]
+    tess = res["tess"]
+    perm, off = tess["perm"], tess["offsets"]
+    A = case["x"]["dense"][np.ix_(perm, perm)]
+    nbr, cnt = metrics.padded_neighbours(tess["nbrs"], 9)
+    Bg = metrics.blocks_from_flat(g["bnear"], g["nf_off"], nbr, cnt, off, 9)
+    rec = dict(res)
+    rec.update(U=g["u"], V=g["v"], coupling=g["at"], nearfield=Bg)
+    Ar = orc.assemble(rec)
+    assert np.linalg.norm(A - Ar) / np.linalg.norm(A) <= 1e-12
+
+
+def test_host_buffer_entry_point_matches(case):
+    tb = _tb()
+    g, x = case["gpu"], case["x"]
+    o = tb.tblr_compress_host(g["prob"], x["pts"], x["T"], x["G"], x["H"], dense=x["dense"])
+    assert np.array_equal(o["perm"].numpy(), g["perm"])
+    assert np.array_equal(o["u"].numpy(), g["u"])
+    assert np.array_equal(o["at"].numpy(), g["at"])
+    assert np.array_equal(o["bnear"].numpy()[:o["bnear_size"]], g["bnear"])
