@@ -47,6 +47,7 @@ extern "C" {
 #define TBLR_ECUDA        -2  /* a CUDA runtime call or launch failed */
 #define TBLR_EUNSUPPORTED -3  /* valid but not implemented (e.g. a size beyond a kernel's limit) */
 #define TBLR_EWORKSPACE   -4  /* caller workspace or output capacity too small */
+#define TBLR_ETIMEOUT     -5  /* a device-side wait gave up (see tblr_device_timeouts) */
 
 /* Operator kinds (§7.1 and explicit matrices). */
 #define TBLR_KERNEL_LAPLACE2D 1  /* A_pq = log|x_p - x_q|, A_pp = 0 (§7.1)      */
@@ -233,6 +234,13 @@ int tblr_compress_host(const tblr_problem *prob, const double *points_h,
                        double *bnear_h, int64_t bnear_capacity, int64_t *bnear_size,
                        void *stream);
 int tblr_release_device_cache(void);
+
+/* Device-side waits of the tensor-core kernels (mbarrier pipelines) are
+ * bounded: a wait that does not complete within ~0.5 s abandons its launch,
+ * whose output is then undefined, and increments a per-device counter.  This
+ * call synchronises the device, stores the counter in *count, resets it, and
+ * returns TBLR_OK (or TBLR_ECUDA). */
+int tblr_device_timeouts(unsigned int *count /* host */);
 
 #ifdef __cplusplus
 }

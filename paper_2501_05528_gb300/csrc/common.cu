@@ -87,6 +87,7 @@ extern "C" const char *tblr_status_string(int status) {
     case TBLR_ECUDA: return "CUDA error";
     case TBLR_EUNSUPPORTED: return "unsupported";
     case TBLR_EWORKSPACE: return "workspace or capacity too small";
+    case TBLR_ETIMEOUT: return "device-side wait timed out";
   }
   return "unknown status";
 }

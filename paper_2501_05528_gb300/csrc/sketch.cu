@@ -3,10 +3,9 @@
 //
 // FP64 apply design (GB300 runs DFMA at ~1.2 TFLOP/s, so the kernel is bound
 // by the FP64 pipe, not by memory): a CTA owns BM = 16 rows of Y and up to
-// 256 * CPT columns; each step generates the BM x BK tile of A once (one entry
-// per thread; a log or rsqrt costs ~36 DFMA) and contracts it with the
-// BK x (256 CPT) slice of X staged in shared memory, so every generated entry
-// feeds up to 1280 DFMAs.
+// 256 * CPT columns; each K step generates the BM x BK tile of A once (a log
+// or rsqrt costs ~36 DFMA) and contracts it with the BK x (256 CPT) slice of X
+// staged in shared memory, so every generated entry feeds up to 1280 DFMAs.
 #include "common.cuh"
 #include "mixed.cuh"
 
@@ -47,16 +46,26 @@ __global__ void __launch_bounds__(256) test_matrices_kernel(
   }
 }
 
-constexpr int kBM = 16, kBK = 16, kThreads = 256;
+constexpr int kBM = 16, kBK = 8, kThreads = 256;
 
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Two-stage pipeline: while the FP64 pipe contracts stage `cur`, the X slice of
+// the next K step streams into the other stage with cp.async and the next
+// kernel tile is generated.
 template <class Op, int CPT>
 __global__ void __launch_bounds__(kThreads, 1)
     apply_fp64_kernel(Op op, const double *__restrict__ xt, int64_t n, int64_t ncols,
                       double *__restrict__ y, int64_t ldy) {
   extern __shared__ double sm[];
   constexpr int NT = kThreads * CPT;
-  double *As = sm;               // [kBK][kBM]
-  double *Xs = sm + kBK * kBM;   // [kBK][NT]
+  double *As = sm;                   // [2][kBK][kBM]
+  double *Xs = sm + 2 * kBK * kBM;   // [2][kBK][NT]
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t row0 = (int64_t)blockIdx.x * kBM;
   const int64_t col0 = (int64_t)blockIdx.y * NT;
@@ -64,51 +73,65 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
   for (int s = 0; s < CPT; ++s) active[s] = col0 + kThreads * s + warp * 32 < ncols;
 
+  auto stage_in = [&](int buf, int64_t k0) {
+#pragma unroll
+    for (int s = 0; s < CPT; ++s) {
+      const int cl = tid + kThreads * s;
+      const int64_t c = col0 + cl;
+      double *dst = Xs + buf * kBK * NT + cl;
+#pragma unroll
+      for (int kk = 0; kk < kBK; ++kk) {
+        if (c < ncols && k0 + kk < n)
+          cp_async8(dst + kk * NT, xt + c * n + k0 + kk);
+        else
+          dst[kk * NT] = 0.0;
+      }
+    }
+    cp_async_commit();
+    if (tid < kBM * kBK) {
+      const int r = tid % kBM, kk = tid / kBM;
+      const int64_t gi = row0 + r, gj = k0 + kk;
+      double v = 0.0;
+      if (gi < n && gj < n) v = op(gi, gj);
+      As[buf * kBK * kBM + kk * kBM + r] = v;
+    }
+  };
+
   double acc[kBM][CPT];
 #pragma unroll
   for (int r = 0; r < kBM; ++r)
 #pragma unroll
     for (int s = 0; s < CPT; ++s) acc[r][s] = 0.0;
 
-  for (int64_t k0 = 0; k0 < n; k0 += kBK) {
-    __syncthreads();
-    {
-      const int r = tid % kBM, kk = tid / kBM;  // kBM * kBK == kThreads
-      const int64_t gi = row0 + r, gj = k0 + kk;
-      double v = 0.0;
-      if (gi < n && gj < n) v = op(gi, gj);
-      As[kk * kBM + r] = v;
-    }
+  const int64_t nsteps = (n + kBK - 1) / kBK;
+  stage_in(0, 0);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int64_t step = 0; step < nsteps; ++step) {
+    const int cur = (int)(step & 1);
+    if (step + 1 < nsteps) stage_in(cur ^ 1, (step + 1) * kBK);
+    const double *Ac = As + cur * kBK * kBM;
+    const double *Xc = Xs + cur * kBK * NT;
 #pragma unroll
-    for (int s = 0; s < CPT; ++s) {
-      const int cl = tid + kThreads * s;
-      const int64_t c = col0 + cl;
-#pragma unroll
-      for (int kk = 0; kk < kBK; ++kk) {
-        double v = 0.0;
-        if (c < ncols && k0 + kk < n) v = __ldg(xt + c * n + k0 + kk);
-        Xs[kk * NT + cl] = v;
-      }
-    }
-    __syncthreads();
-#pragma unroll 4
     for (int kk = 0; kk < kBK; ++kk) {
       double a[kBM];
 #pragma unroll
       for (int r = 0; r < kBM; r += 2) {
-        const double2 t = *reinterpret_cast<const double2 *>(As + kk * kBM + r);
+        const double2 t = *reinterpret_cast<const double2 *>(Ac + kk * kBM + r);
         a[r] = t.x;
         a[r + 1] = t.y;
       }
 #pragma unroll
       for (int s = 0; s < CPT; ++s) {
         if (active[s]) {
-          const double x = Xs[kk * NT + tid + kThreads * s];
+          const double x = Xc[kk * NT + tid + kThreads * s];
 #pragma unroll
           for (int r = 0; r < kBM; ++r) acc[r][s] = fma(a[r], x, acc[r][s]);
         }
       }
     }
+    cp_async_wait_all();
+    __syncthreads();
   }
 #pragma unroll
   for (int s = 0; s < CPT; ++s) {
@@ -125,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <class Op, int CPT>
 int launch_apply_fp64_cpt(const Op &op, const double *xt, int64_t n, int64_t ncols, double *y,
                           int64_t ldy, cudaStream_t s) {
-  const size_t smem = sizeof(double) * (kBK * kBM + kBK * kThreads * CPT);
+  const size_t smem = sizeof(double) * 2 * (kBK * kBM + kBK * kThreads * CPT);
   auto kern = apply_fp64_kernel<Op, CPT>;
   TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((unsigned)cdiv(n, kBM), (unsigned)cdiv(ncols, kThreads * CPT));

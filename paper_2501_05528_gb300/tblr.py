@@ -15,7 +15,7 @@ import torch
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtblr.so")
 
-TBLR_OK, TBLR_EINVAL, TBLR_ECUDA, TBLR_EUNSUPPORTED, TBLR_EWORKSPACE = 0, -1, -2, -3, -4
+TBLR_OK, TBLR_EINVAL, TBLR_ECUDA, TBLR_EUNSUPPORTED, TBLR_EWORKSPACE, TBLR_ETIMEOUT = 0, -1, -2, -3, -4, -5
 KERNELS = {"laplace2d": 1, "laplace3d": 2, "dense": 3}
 FP64, MIXED = 0, 1
 NEARFIELD_PROBE, NEARFIELD_EXACT = 0, 1
@@ -77,6 +77,7 @@ _SIGNATURES = {
     "tblr_compress_host": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                           _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
     "tblr_release_device_cache": (ctypes.c_int, []),
+    "tblr_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
 }
 
 _lib = None
@@ -255,6 +256,13 @@ def tblr_nearfield(prob, lay, u, at, v, ranks, nf_off, m_max: int, total: int, d
                                 _p(ranks), _p(nf_off), m_max, _p(bnear), _p(ws), nbytes, _stream()),
            "tblr_nearfield")
     return bnear
+
+
+def tblr_device_timeouts() -> int:
+    """Synchronise the device; return and reset the count of timed-out device waits."""
+    out = ctypes.c_uint(0)
+    _check(lib().tblr_device_timeouts(ctypes.byref(out)), "tblr_device_timeouts")
+    return int(out.value)
 
 
 class Compressed:

@@ -1,0 +1,83 @@
+"""GPU parity of the mixed-precision (tcgen05, split FP16, FP32 accumulation) path.
+
+Bound: the split-precision apply and the whole compression built on it must
+match the FP64 oracle within 1e-6 relative Frobenius error (the stated bound
+for the mixed path).  The dropped lo*lo term contributes ~2^-22, FP16
+rounding of each half ~2^-23 relative per product, and the FP32 tensor-core
+accumulation is flushed every 64 points into compensated sums, so the measured
+error is expected near 1e-7.  Cases have ragged row and column tails.
+"""
+import numpy as np
+import pytest
+
+from oracle import tagging as orc
+from paper_2501_05528_gb300 import inputs
+from tests import metrics
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+MIXED_BOUND = 1e-6
+
+
+def _tb():
+    from paper_2501_05528_gb300 import tblr
+    return tblr
+
+
+APPLY_CASES = [
+    ("laplace2d", 2, (6, 6), 3001, 468),
+    ("laplace3d", 3, (4, 4, 4), 2501, 200),
+    ("laplace2d", 2, (3, 3), 130, 16),
+]
+
+
+@pytest.mark.parametrize("kind,d,grid,n,ncols", APPLY_CASES)
+def test_mixed_apply_matches_fp64_oracle(kind, d, grid, n, ncols):
+    tb = _tb()
+    pts = inputs.uniform_points(n, d, seed=n)
+    X = np.random.default_rng(n + 1).standard_normal((n, ncols))
+    prob = tb.make_problem(d, kind, n, grid, (0.0,) * d, (1.0,) * d, 4, 10, 0)
+    dev = torch.device("cuda")
+    lay = tb.tblr_tessellate(prob, torch.as_tensor(pts, device=dev))
+    perm = lay.perm.cpu().numpy()
+    xt = torch.as_tensor(np.ascontiguousarray(X[perm].T), device=dev)   # K-major, box-major rows
+    y_mixed = tb.tblr_apply(prob, lay, xt, ncols, precision=tb.MIXED).cpu().numpy()
+    assert tb.tblr_device_timeouts() == 0
+    y_fp64 = tb.tblr_apply(prob, lay, xt, ncols, precision=tb.FP64).cpu().numpy()
+    op = orc.KernelOperator(kind, pts[perm])
+    ref = op.apply(X[perm])
+    err = metrics.rel(y_mixed, ref)
+    print(f"mixed apply {kind} n={n} ncols={ncols}: rel err {err:.3e}")
+    assert err < MIXED_BOUND
+    assert metrics.rel(y_fp64, ref) < 1e-12
+    # every row and column (including the ragged tails) is accurate
+    row_err = np.linalg.norm(y_mixed - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert row_err.max() < 10 * MIXED_BOUND
+
+
+@pytest.mark.parametrize("kind,d,grid,n,k,e", [("laplace2d", 2, (6, 6), 3001, 8, 3),
+                                              ("laplace3d", 3, (4, 4, 4), 2501, 6, 1)])
+def test_mixed_compression_within_bound(kind, d, grid, n, k, e):
+    tb = _tb()
+    pts = inputs.uniform_points(n, d, seed=7 * n)
+    b = int(np.prod(grid))
+    ell = orc.tag_columns(d, e)
+    T, G, H = inputs.tagging_draws(b, ell, n, k + 10, seed=7 * n + 1)
+    lo, hi = (0.0,) * d, (1.0,) * d
+    ref = orc.reconstruct_tag(pts, grid, lo, hi, kind, T, G, H, k, 10)
+    prob = tb.make_problem(d, kind, n, grid, lo, hi, k, 10, e, precision=tb.MIXED)
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(a, device=dev)
+    out = tb.compress(prob, t(pts), t(T), t(G), t(H))
+    assert tb.tblr_device_timeouts() == 0
+    tess = ref["tess"]
+    s3 = 3 ** d
+    nbr, cnt = metrics.padded_neighbours(tess["nbrs"], s3)
+    off = tess["offsets"]
+    B = metrics.blocks_from_flat(out.bnear.cpu().numpy(), out.nf_off.cpu().numpy(), nbr, cnt, off, s3)
+    rep = dict(U=out.u.cpu().numpy(), V=out.v.cpu().numpy(), At=out.at.cpu().numpy(), B=B)
+    rep_o = dict(U=ref["U"], V=ref["V"], At=ref["coupling"], B=ref["nearfield"])
+    err = metrics.ublr_difference(off, nbr, cnt, s3, ref["ranks"], rep, rep_o)
+    print(f"mixed compression {kind}: rel err vs FP64 oracle {err:.3e}")
+    assert err < MIXED_BOUND
