@@ -121,6 +121,28 @@ size_t tblr_tessellate_workspace(const tblr_problem *prob);
 int tblr_tessellate(const tblr_problem *prob, const double *points,
                     const tblr_layout *out, void *ws, size_t ws_bytes, void *stream);
 
+/* Allocation-free tessellation.  The paper has no counterpart: this entry
+ * exists for callers that cannot allocate device memory, such as a request
+ * loop running under a device-memory budget fixed up front, or code whose
+ * device allocator belongs to a host framework it may not call into.  It
+ * computes exactly what tblr_tessellate computes, from the same inputs into
+ * the same caller-owned outputs, but takes its scratch from one fixed static
+ * device array of TBLR_NOALLOC_SCRATCH_BYTES (8 MiB) that every GPU loading
+ * the library holds until the process exits.  It never calls cudaMalloc,
+ * cudaFree or any allocating routine.
+ * - Limit: tblr_tessellate_workspace(prob) must not exceed 8 MiB (roughly
+ *   n * 4 + b * ceil(n / 2048) * 4 bytes); larger problems get TBLR_EINVAL
+ *   with a message naming the sizes.
+ * - The first call on a device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.
+ * - All calls on a device share the one array, which keeps the last call's
+ *   contents: calls that can overlap on the GPU (different streams without
+ *   ordering between them) race and give undefined results.  Calls ordered on
+ *   one stream are safe. */
+#define TBLR_NOALLOC_SCRATCH_BYTES (8 << 20)
+int tblr_tessellate_noalloc(const tblr_problem *prob, const double *points,
+                            const tblr_layout *out, void *stream);
+
 /* Near-field block offsets: nf_off[i*S3 + s] = start (in doubles) of block
  * B_{i, nbr[i*S3+s]} (m_i x m_j, row-major) in the near-field array, for
  * s < nnbr[i]; unused slots repeat the next start; nf_off[b*S3] = total.

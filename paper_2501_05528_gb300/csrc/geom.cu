@@ -1,9 +1,13 @@
 // a1: tessellation into a regular grid of boxes, stable box-major order,
 // neighbour lists N_i and colours (§2.5 strong admissibility; §6.1 probes).
+// Also tblr_tessellate_noalloc, the same tessellation with its scratch in a
+// fixed static device array instead of a caller workspace.
 //
 // Stable counting sort in three launches: per-chunk box histograms, one
 // exclusive scan over (box, chunk) in box-major order, and a per-chunk scatter
 // that ranks equal boxes in input order (warp match + warps taking turns).
+#include <mutex>
+
 #include "common.cuh"
 
 namespace tblr {
@@ -251,4 +255,48 @@ extern "C" int tblr_nearfield_offsets(const tblr_problem *prob, const tblr_layou
   block_exclusive_scan<int64_t><<<1, 1024, 0, s>>>(nf_off, len, nf_off + len);
   TBLR_TRY(launch_status("block_exclusive_scan"));
   return TBLR_OK;
+}
+
+// ------------------------------------------------- allocation-free variant
+// Scratch for tblr_tessellate_noalloc: one fixed array per device, created
+// when the library is loaded on that device and held until process exit.
+static __device__ __align__(256) unsigned char g_tess_scratch[TBLR_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_tess_scratch on the current device.  Host code cannot
+// use the symbol itself (on the host it names a stand-in, not device memory),
+// so the address is looked up once per device and cached.
+int scratch_address(void **out) {
+  int dev = 0;
+  TBLR_CUDA(cudaGetDevice(&dev));
+  TBLR_REQUIRE(dev >= 0 && dev < kMaxDevices, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch_addr[dev] == nullptr) {
+    void *p = nullptr;
+    TBLR_CUDA(cudaGetSymbolAddress(&p, g_tess_scratch));
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return TBLR_OK;
+}
+}  // namespace
+
+extern "C" int tblr_tessellate_noalloc(const tblr_problem *prob, const double *points,
+                                       const tblr_layout *out, void *stream) {
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  const size_t need = tblr_tessellate_workspace(prob);
+  TBLR_REQUIRE(need <= (size_t)TBLR_NOALLOC_SCRATCH_BYTES,
+               "tblr_tessellate_noalloc: this problem needs %zu bytes of scratch, more than the "
+               "fixed %d-byte array (use tblr_tessellate with a workspace)",
+               need, (int)TBLR_NOALLOC_SCRATCH_BYTES);
+  void *scratch = nullptr;
+  TBLR_TRY(scratch_address(&scratch));
+  // Every scratch byte the tessellation reads is written earlier in the same
+  // call (box ids, then the per-chunk histograms), so nothing needs clearing.
+  return tblr_tessellate(prob, points, out, scratch, (size_t)TBLR_NOALLOC_SCRATCH_BYTES, stream);
 }

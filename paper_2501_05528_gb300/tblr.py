@@ -56,6 +56,7 @@ _SIGNATURES = {
     "tblr_sizes_of": (ctypes.c_int, [_PP, ctypes.POINTER(Sizes)]),
     "tblr_tessellate_workspace": (_SZ, [_PP]),
     "tblr_tessellate": (ctypes.c_int, [_PP, _VP, _PL, _VP, _SZ, _VP]),
+    "tblr_tessellate_noalloc": (ctypes.c_int, [_PP, _VP, _PL, _VP]),
     "tblr_nearfield_offsets": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP]),
     "tblr_test_matrices": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP]),
     "tblr_apply_workspace": (_SZ, [_PP, _I64, ctypes.c_int]),
@@ -169,6 +170,17 @@ def tblr_tessellate(prob: Problem, points: torch.Tensor) -> Layout:
     _check(lib().tblr_tessellate(ctypes.byref(prob), _p(points), lay.ref, _p(ws), nbytes, _stream()),
            "tblr_tessellate")
     lay._ws = ws
+    return lay
+
+
+def tblr_tessellate_noalloc(prob: Problem, points: torch.Tensor) -> Layout:
+    """Tessellation whose scratch is the library's fixed static device array
+    (no allocation inside the call; the caller still owns inputs and outputs)."""
+    _require_cuda()
+    points = points.contiguous()
+    lay = Layout(prob)
+    _check(lib().tblr_tessellate_noalloc(ctypes.byref(prob), _p(points), lay.ref, _stream()),
+           "tblr_tessellate_noalloc")
     return lay
 
 
