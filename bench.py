@@ -44,6 +44,13 @@ WORKLOADS = {
     # same recipe, 16,384 points on 8 x 8 boxes: the small case used for ncu captures
     "laplace2d_n16384": dict(d=2, n=16384, grid=(8, 8), k=32, p=10, e=3, kernel="laplace2d",
                              seed=0x7A660012),
+    # 3D Laplace, jittered 64^3 lattice (jitter U[-h/4, h/4]), 8 x 8 x 8 boxes of 512 points,
+    # k = 64; run with --precision mixed
+    "laplace3d_n262144": dict(d=3, n=262144, grid=(8, 8, 8), k=64, p=10, e=3, kernel="laplace3d",
+                              seed=0x7A660003, lattice=64, cpu_boxes=1),
+    # same recipe on a 32^3 lattice, 4 x 4 x 4 boxes of 512 points
+    "laplace3d_n32768": dict(d=3, n=32768, grid=(4, 4, 4), k=64, p=10, e=3, kernel="laplace3d",
+                             seed=0x7A660013, lattice=32, cpu_boxes=2),
 }
 
 
@@ -55,7 +62,10 @@ def env_rank():
 def make_inputs(w, rank=0):
     from paper_2501_05528_gb300 import inputs
     d = w["d"]
-    pts = inputs.uniform_points(w["n"], d, seed=w["seed"] + 7919 * rank)
+    if "lattice" in w:
+        pts = inputs.jittered_lattice(w["lattice"], d, 0.25, seed=w["seed"] + 7919 * rank)
+    else:
+        pts = inputs.uniform_points(w["n"], d, seed=w["seed"] + 7919 * rank)
     b = int(np.prod(w["grid"]))
     ell = 3 ** d + 1 + w["e"]
     T, G, H = inputs.tagging_draws(b, ell, w["n"], w["k"] + w["p"], seed=w["seed"] + 1 + 7919 * rank)
@@ -238,7 +248,8 @@ class Runner:
                       s), "col U")
         ck(L.tblr_col(P, lay.ref, p(self.R), p(o.v), p(o.ranks), p(self.colws), self.colws.numel(),
                       s), "col V")
-        ck(L.tblr_coupling(P, lay.ref, None, p(o.u), p(o.v), p(o.ranks), p(o.at), s), "coupling")
+        ck(L.tblr_coupling(P, lay.ref, None, p(o.u), p(o.v), p(o.ranks), m_max, p(o.at), s),
+           "coupling")
         ck(L.tblr_nearfield(P, lay.ref, None, p(o.u), p(o.at), p(o.v), p(o.ranks), p(o.nf_off),
                             m_max, p(o.bnear), p(self.nfws), self.nfws.numel(), s), "nearfield")
 
@@ -265,6 +276,28 @@ def roofline(w, achieved, sketch_ms, traffic):
             "peak_source": f"{src} dense bf16 burst (fp16 runs at the same rate)",
             "executed_tflops": 3.0 * achieved, "executed_frac": 3.0 * achieved / peak,
             "sketch_ms": sketch_ms}
+
+
+def mixed_vs_fp64(tb, torch, w, run):
+    """Full-matrix relative Frobenius difference between the mixed-precision result
+    and the FP64 GPU result on the same inputs (the FP64 path matches the CPU
+    oracle to 1e-10 in the parity tests), computed on the host."""
+    from paper_2501_05528_gb300 import metrics
+    d = w["d"]
+    prob64 = tb.make_problem(d, w["kernel"], w["n"], w["grid"], (0.0,) * d, (1.0,) * d, w["k"],
+                             w["p"], w["e"], precision=tb.FP64)
+    ref = tb.compress(prob64, run.pts, run.T, run.G, run.H)
+    torch.cuda.synchronize()
+    h = lambda t: t.cpu().numpy()
+    off, nbr, nnbr = h(run.lay.offsets), h(run.lay.nbr), h(run.lay.nnbr)
+    s3 = run.sz.s3
+    reps = []
+    for o in (run.out, ref):
+        B = metrics.blocks_from_flat(h(o.bnear), h(o.nf_off), nbr, nnbr, off, s3)
+        reps.append(dict(U=h(o.u), V=h(o.v), At=h(o.at), B=B))
+    err = metrics.ublr_difference_all(off, nbr, nnbr, s3, h(run.out.ranks), reps[0], reps[1])
+    return {"relerr_vs_fp64": err, "bound": 1e-6, "within_bound": bool(err <= 1e-6),
+            "reference": "FP64 GPU path on the same inputs, full matrix, Frobenius"}
 
 
 def run_gpu(args, w):
@@ -346,6 +379,10 @@ def run_gpu(args, w):
         dist.all_reduce(temax, op=dist.ReduceOp.MAX)
     e2e_value = e2e_steps * world / float(temax.item())
 
+    accuracy = None
+    if rank == 0 and w.get("precision", 0) == 1 and not args.no_fp64_check:
+        accuracy = mixed_vs_fp64(tb, torch, w, run)
+
     result = None
     if rank == 0:
         flops = 2.0 * w["n"] * w["n"] * sz.sketch_cols
@@ -355,7 +392,7 @@ def run_gpu(args, w):
                        at=run.out.at.cpu().numpy())
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            boxes = sample_boxes(w["grid"], args.cpu_sample_boxes)
+            boxes = sample_boxes(w["grid"], w.get("cpu_boxes", args.cpu_sample_boxes))
             secs, frac, sample = oracle_sample(w, pts, T, G, H, boxes)
             relerr = compare_sample(sample, gpu_res)
             cpu = {"value": frac / secs, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
@@ -386,6 +423,8 @@ def run_gpu(args, w):
             "cpu_baseline": cpu,
             "clocks": sampler.summary(),
         }
+        if accuracy is not None:
+            result["accuracy"] = accuracy
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -397,7 +436,7 @@ def run_reference(args, w):
     if rank != 0:
         return None
     pts, T, G, H = make_inputs(w, 0)
-    boxes = sample_boxes(w["grid"], args.cpu_sample_boxes)
+    boxes = sample_boxes(w["grid"], w.get("cpu_boxes", args.cpu_sample_boxes))
     for _ in range(args.warmup):
         oracle_sample(w, pts, T, G, H, boxes)
     times = []
@@ -429,6 +468,8 @@ def main():
     ap.add_argument("--workload", default="laplace2d_n65536", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample-boxes", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true",
+                    help="skip the mixed-vs-FP64 accuracy check of the mixed path")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="sketch contraction precision (everything else stays FP64)")
     ap.add_argument("--traffic", type=float, default=None,

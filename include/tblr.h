@@ -23,9 +23,10 @@
  * - Every call returns TBLR_OK (0) or a negative status.  Argument errors are
  *   detected on the host before anything is enqueued; CUDA errors are reported
  *   as TBLR_ECUDA.  tblr_last_error() gives a message for the calling thread.
- * - Floating point: FP64 unless the problem selects TBLR_MIXED, in which case
- *   only the sketch contraction (tblr_sketch) runs in split FP16 with FP32
- *   accumulation; everything else stays FP64.
+ * - Floating point: FP64 unless the problem selects TBLR_MIXED.  Then the
+ *   sketch contraction (tblr_sketch, tblr_apply) runs on the tensor cores in
+ *   split FP16 with FP32 accumulation, coupling and near field run on the FP32
+ *   pipes with compensated sums, and tag decode, combine and col stay FP64.
  *
  * Symbols used below: d dimension (1..3); n points; b boxes (product of grid);
  * ell = 3^d + 1 + e tag columns; r = k + p; C = ell * r sketch columns per side;
@@ -54,9 +55,9 @@ extern "C" {
 #define TBLR_KERNEL_LAPLACE3D 2  /* A_pq = 1/(4 pi |x_p - x_q|), A_pp = 0       */
 #define TBLR_KERNEL_DENSE     3  /* A given explicitly, n x n, original order   */
 
-/* Precision of the sketch contraction (the other steps are FP64 always). */
+/* Precision mode (see "Floating point" above). */
 #define TBLR_FP64  0
-#define TBLR_MIXED 1  /* FP16 hi/lo split operands, FP32 tensor-core accumulation */
+#define TBLR_MIXED 1  /* split-FP16 tensor-core sketch; FP32 coupling and near field */
 
 /* Near-field reading (§6.1): the paper's identity probe, or the exact block. */
 #define TBLR_NEARFIELD_PROBE 0  /* B_ij = sum_{c: colour(c)=colour(j)} (A_ic - U_i At_ic V_c^T)(:, 0:m_j) */
@@ -208,9 +209,12 @@ int tblr_col(const tblr_problem *prob, const tblr_layout *lay, const double *s,
 
 /* ---------------------------------- a7: coupling (Table 1 step 2, §2.5)
  * Atilde_ij = U_i^T A_ij V_j for ALL box pairs: at[((i*b + j)*k + a)*k + c],
- * zero outside a < k_i, c < k_j.  u, v: [n*k]; ranks: [b]. */
+ * zero outside a < k_i, c < k_j.  u, v: [n*k]; ranks: [b]; m_max = max_i m_i
+ * (as returned by tblr_nearfield_offsets).  FP64, or with TBLR_MIXED on the
+ * FP32 pipes (double-float coordinates, compensated sums, ~1e-7 relative).
+ * Limits: k <= 64; mixed: m_max <= ~780. */
 int tblr_coupling(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
-                  const double *u, const double *v, const int32_t *ranks,
+                  const double *u, const double *v, const int32_t *ranks, int32_t m_max,
                   double *at, void *stream);
 
 /* ------------------ a8: near field (Table 1 step 3; §6.1 eq. sparse_struct_ids)

@@ -61,7 +61,7 @@ extern "C" int tblr_compress(const tblr_problem *prob, const tblr_layout *lay, c
   TBLR_TRY(tblr_col(prob, lay, S, u, ranks, colws, w.col, stream));
   TBLR_TRY(tblr_col(prob, lay, R, v, ranks, colws, w.col, stream));
   // Step II (Table 1): Atilde = U^T (A V).
-  TBLR_TRY(tblr_coupling(prob, lay, dense, u, v, ranks, at, stream));
+  TBLR_TRY(tblr_coupling(prob, lay, dense, u, v, ranks, m_max, at, stream));
   // Step III (Table 1): near field from the identity probes.
   return tblr_nearfield(prob, lay, dense, u, at, v, ranks, nf_off, m_max, bnear, nfws, w.nf, stream);
 }

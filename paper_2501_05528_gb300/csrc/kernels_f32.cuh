@@ -1,0 +1,42 @@
+// FP32 kernel-matrix entries from double-float coordinates, shared by the
+// mixed-precision kernels.  A coordinate x is carried as hi = fl32(x) and
+// lo = fl32(x - hi), so differences (hi_p - hi_q) + (lo_p - lo_q) keep ~48
+// bits: the hi difference is exact for close points (Sterbenz) and the lo
+// parts restore the rest for far ones.  Entry error is ~2^-23 relative.
+#pragma once
+#include "common.cuh"
+
+namespace tblr {
+
+template <int KERNEL>
+__device__ __forceinline__ float entry_f32(const float (&ph)[3], const float (&pl)[3],
+                                           const float (&qh)[3], const float (&ql)[3]) {
+  if (KERNEL == TBLR_KERNEL_LAPLACE2D) {
+    const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
+    const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
+    const float r2 = fmaf(dx, dx, dy * dy);
+    return 0.34657359027997264f * __log2f(r2);  // 0.5 ln(2) log2(r^2) = log r
+  } else {
+    const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
+    const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
+    const float dz = (ph[2] - qh[2]) + (pl[2] - ql[2]);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    return 0.07957747154594767f * rsqrtf(r2);  // 1 / (4 pi r)
+  }
+}
+
+// Split one FP64 coordinate into its double-float pair.
+__device__ __forceinline__ void split_coord(double x, float &hi, float &lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// Kahan-compensated accumulation: sum ~ hi - c.
+__device__ __forceinline__ void kahan_add(float &hi, float &c, float v) {
+  const float y = v - c;
+  const float t = hi + y;
+  c = (t - hi) - y;
+  hi = t;
+}
+
+}  // namespace tblr

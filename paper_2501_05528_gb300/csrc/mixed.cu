@@ -24,6 +24,7 @@
 
 #include <algorithm>
 
+#include "kernels_f32.cuh"
 #include "mixed.cuh"
 #include "tc_utils.cuh"
 
@@ -79,25 +80,6 @@ __device__ __forceinline__ bool wait_or_abort(Smem &S, volatile int *status, uin
       S.abort = 1;
       return false;
     }
-  }
-}
-
-// Kernel entry in FP32 from double-float coordinates (the differences of the
-// hi parts are exact for close points; the lo parts restore ~48-bit inputs).
-template <int KERNEL>
-__device__ __forceinline__ float entry_f32(const float (&ph)[3], const float (&pl)[3],
-                                           const float (&qh)[3], const float (&ql)[3]) {
-  if (KERNEL == TBLR_KERNEL_LAPLACE2D) {
-    const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
-    const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
-    const float r2 = fmaf(dx, dx, dy * dy);
-    return 0.34657359027997264f * __log2f(r2);  // 0.5 ln(2) log2(r^2) = log r
-  } else {
-    const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
-    const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
-    const float dz = (ph[2] - qh[2]) + (pl[2] - ql[2]);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    return 0.07957747154594767f * rsqrtf(r2);  // 1 / (4 pi r)
   }
 }
 

@@ -4,6 +4,7 @@
 // A's blocks are regenerated tile by tile; A V and the probe products are
 // never stored (V is block diagonal, so (A V)(I_i, block j) = A_ij V_j).
 #include "common.cuh"
+#include "recon_mixed.cuh"
 
 namespace tblr {
 namespace {
@@ -178,14 +179,17 @@ __global__ void __launch_bounds__(kThreads) nf_block_kernel(
 using namespace tblr;
 
 extern "C" int tblr_coupling(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
-                             const double *u, const double *v, const int32_t *ranks, double *at,
-                             void *stream) {
+                             const double *u, const double *v, const int32_t *ranks,
+                             int32_t m_max, double *at, void *stream) {
   Prob P;
   TBLR_TRY(check_problem(prob, &P));
   TBLR_TRY(check_layout(P, lay));
   TBLR_REQUIRE(u && v && ranks && at, "u, v, ranks and at must be non-NULL");
   TBLR_REQUIRE(P.k <= kKMax, "coupling supports k <= %d", kKMax);
+  TBLR_REQUIRE(m_max >= 0, "m_max must be >= 0");
   cudaStream_t s = as_stream(stream);
+  if (P.precision == TBLR_MIXED && symmetric_kernel(P.kernel))
+    return coupling_mixed(P, lay, u, v, ranks, at, m_max, s);
   const size_t smem = sizeof(double) * (kT * (kT + 1) + 3 * kT * P.k + P.k * P.k);
   return with_operator(P, lay, dense, 0, [&](auto op) {
     auto kern = coupling_kernel<decltype(op)>;
@@ -199,6 +203,8 @@ extern "C" int tblr_coupling(const tblr_problem *prob, const tblr_layout *lay, c
 extern "C" size_t tblr_nearfield_workspace(const tblr_problem *prob, int32_t m_max) {
   Prob P;
   if (check_problem(prob, &P) != TBLR_OK || m_max < 0) return 0;
+  if (P.precision == TBLR_MIXED && symmetric_kernel(P.kernel))
+    return nearfield_mixed_workspace(P, m_max);
   return align256(sizeof(double) * P.b * P.s3 * P.k * (size_t)m_max);
 }
 
@@ -216,6 +222,8 @@ extern "C" int tblr_nearfield(const tblr_problem *prob, const tblr_layout *lay, 
   TBLR_REQUIRE(ws != nullptr && ws_bytes >= tblr_nearfield_workspace(prob, m_max),
                "nearfield workspace too small");
   cudaStream_t s = as_stream(stream);
+  if (P.precision == TBLR_MIXED && symmetric_kernel(P.kernel))
+    return nearfield_mixed(P, lay, u, at, v, nf_off, m_max, bnear, ws, s);
   double *M = static_cast<double *>(ws);
   const size_t smem = sizeof(int) * P.b;
   const dim3 grid((unsigned)P.b, (unsigned)P.s3);

@@ -1,6 +1,7 @@
-"""Comparison helpers shared by the parity tests (test infrastructure).
+"""Accuracy metrics between two compressed uniform-BLR representations.
 
-They compare two compressed representations; neither side's arithmetic lives
+Used by the parity tests and by the benchmark to state the error of a
+compression against a reference one; none of the compression arithmetic lives
 here.  For a far block the two low-rank products are expressed in a joint
 orthonormal basis: with Q_U = orth([U1, U2]) and Q_V = orth([V1, V2]),
   ||U1 A1 V1^T - U2 A2 V2^T||_F = ||C1 A1 D1^T - C2 A2 D2^T||_F,
@@ -91,3 +92,48 @@ def padded_neighbours(nbrs, s3):
         arr[i * s3:i * s3 + len(lst)] = lst
         cnt[i] = len(lst)
     return arr, cnt
+
+
+def ublr_difference_all(off, nbr, nnbr, s3, ranks, rep1, rep2):
+    """ublr_difference over every box pair, vectorised over column boxes.
+
+    Far blocks use the joint-basis identity with all k columns of each basis
+    (columns beyond k_i are zero in both representations, so they add nothing).
+    """
+    b = len(off) - 1
+    k = rep1["U"].shape[1]
+    near = {(i, j) for (i, j, _) in near_pairs(nbr, nnbr, s3)}
+    C1 = np.zeros((b, 2 * k, k))
+    C2 = np.zeros((b, 2 * k, k))
+    E1 = np.zeros((b, 2 * k, k))
+    E2 = np.zeros((b, 2 * k, k))
+    for i in range(b):
+        ri = slice(off[i], off[i + 1])
+        for (X1, X2, D1, D2) in ((rep1["U"], rep2["U"], C1, C2), (rep1["V"], rep2["V"], E1, E2)):
+            M = np.hstack([X1[ri], X2[ri]])
+            if M.shape[0] == 0:
+                continue
+            Q = np.linalg.qr(M)[0]
+            w = Q.shape[1]
+            D1[i, :w] = Q.T @ X1[ri]
+            D2[i, :w] = Q.T @ X2[ri]
+    num = 0.0
+    den = 0.0
+    farmask = np.ones((b, b), dtype=bool)
+    for (i, j) in near:
+        farmask[i, j] = False
+    for i in range(b):
+        js = np.flatnonzero(farmask[i])
+        if len(js):
+            T1 = np.einsum("ab,jbc,jdc->jad", C1[i], rep1["At"][i, js], E1[js], optimize=True)
+            T2 = np.einsum("ab,jbc,jdc->jad", C2[i], rep2["At"][i, js], E2[js], optimize=True)
+            num += float(np.sum((T1 - T2) ** 2))
+            den += float(np.sum(rep2["At"][i, js] ** 2))
+    for (i, j) in near:
+        ri = slice(off[i], off[i + 1])
+        rj = slice(off[j], off[j + 1])
+        D1 = rep1["U"][ri] @ rep1["At"][i, j] @ rep1["V"][rj].T + rep1["B"][(i, j)]
+        D2 = rep2["U"][ri] @ rep2["At"][i, j] @ rep2["V"][rj].T + rep2["B"][(i, j)]
+        num += float(np.sum((D1 - D2) ** 2))
+        den += float(np.sum(D2 ** 2))
+    return float(np.sqrt(num / den)) if den > 0 else float(np.sqrt(num))

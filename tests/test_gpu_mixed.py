@@ -12,7 +12,7 @@ import pytest
 
 from oracle import tagging as orc
 from paper_2501_05528_gb300 import inputs
-from tests import metrics
+from paper_2501_05528_gb300 import metrics
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")

@@ -16,7 +16,7 @@ import pytest
 
 from oracle import tagging as orc
 from paper_2501_05528_gb300 import inputs
-from tests import metrics
+from paper_2501_05528_gb300 import metrics
 
 pytestmark = pytest.mark.gpu
 
@@ -87,8 +87,8 @@ def case(request):
     s, rr = tb.tblr_combine(prob, lay, yz, z)
     u, ranks = tb.tblr_col(prob, lay, s)
     v, ranks_v = tb.tblr_col(prob, lay, rr)
-    at = tb.tblr_coupling(prob, lay, u, v, ranks, dense=dense)
     mm, total = int(m_max.item()), int(nf_off[-1].item())
+    at = tb.tblr_coupling(prob, lay, u, v, ranks, mm, dense=dense)
     bn = tb.tblr_nearfield(prob, lay, u, at, v, ranks, nf_off, mm, total, dense=dense)
     full = tb.tblr_compress(prob, lay, T, G, H, dense=dense)
     torch.cuda.synchronize()

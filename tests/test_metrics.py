@@ -3,7 +3,7 @@ import numpy as np
 
 from oracle import tagging as orc
 from paper_2501_05528_gb300 import inputs
-from tests import metrics
+from paper_2501_05528_gb300 import metrics
 
 
 def _result():
@@ -28,6 +28,7 @@ def test_metric_invariant_under_rotation_and_sensitive():
             At2[i, j][:ki] = Q.T @ res["coupling"][i, j][:ki]
     rot = dict(rep, U=U2, At=At2)
     assert metrics.ublr_difference(off, nbr, cnt, 9, res["ranks"], rot, rep) < 1e-14
+    assert metrics.ublr_difference_all(off, nbr, cnt, 9, res["ranks"], rot, rep) < 1e-14
     A3 = res["coupling"].copy()
     A3[0, 15] *= 1 + 1e-8
     d = metrics.ublr_difference(off, nbr, cnt, 9, res["ranks"], dict(rep, At=A3), rep)
@@ -35,3 +36,5 @@ def test_metric_invariant_under_rotation_and_sensitive():
     p2 = dict(res, coupling=A3)
     ref = np.linalg.norm(orc.assemble(p2) - full) / np.linalg.norm(full)
     assert abs(d - ref) <= 1e-3 * ref
+    d_all = metrics.ublr_difference_all(off, nbr, cnt, 9, res["ranks"], dict(rep, At=A3), rep)
+    assert abs(d_all - ref) <= 1e-3 * ref
