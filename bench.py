@@ -59,6 +59,21 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def reduce_max(value, world, device="cpu"):
+    """Max of a per-rank scalar over all ranks (the slowest rank sets the time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(steps, world, seconds):
+    """Whole-job throughput: every rank ran `steps` independent compressions."""
+    return steps * world / seconds
+
+
 def make_inputs(w, rank=0):
     from paper_2501_05528_gb300 import inputs
     d = w["d"]
@@ -344,11 +359,8 @@ def run_gpu(args, w):
     total_ms = t0.elapsed_time(t1)
     step_ms = [a.elapsed_time(b) for a, b in stp]
     sketch_ms = [a.elapsed_time(b) for a, b in evs]
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    value = args.steps * world / (total_ms / 1e3)
+    total_ms = reduce_max(total_ms, world, "cuda")
+    value = weak_value(args.steps, world, total_ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned host memory)
     pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
@@ -374,10 +386,7 @@ def run_gpu(args, w):
         tb.tblr_compress_host(run.prob, hp, hT, hG, hH, outputs=outs)
     barrier()
     te = time.perf_counter() - te
-    temax = torch.tensor([te], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(temax, op=dist.ReduceOp.MAX)
-    e2e_value = e2e_steps * world / float(temax.item())
+    e2e_value = weak_value(e2e_steps, world, reduce_max(te, world, "cuda"))
 
     accuracy = None
     if rank == 0 and w.get("precision", 0) == 1 and not args.no_fp64_check:

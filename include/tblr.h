@@ -63,6 +63,17 @@ extern "C" {
 #define TBLR_NEARFIELD_PROBE 0  /* B_ij = sum_{c: colour(c)=colour(j)} (A_ic - U_i At_ic V_c^T)(:, 0:m_j) */
 #define TBLR_NEARFIELD_EXACT 1  /* B_ij = A_ij - U_i At_ij V_j^T  (eq. discrepancymatrix) */
 
+/* How tblr_compress forms the samples S_i = sum_j z_ij Y_j(I_i, :).
+ * BLACKBOX: the paper's order - sketch Y = A Omega, Z = A^T Psi with the
+ *   explicit extended test matrices, then decode and combine (Algorithm 2).
+ * TAGGED: decode first, then S = A' G, R = A'^T H with A'(p, q) =
+ *   tau_i(c) A(p, q) for p in I_i, q in I_c (tau_i = T z_i).  Equal to the
+ *   black-box S and R in exact arithmetic (eq. extend_test_mat: Y_j(I_i) =
+ *   sum_c t_cj A_ic G_c), with ell times fewer multiply-adds and near-field
+ *   terms weighted by tau_i(c) ~ 0 instead of cancelling between sketches. */
+#define TBLR_SKETCH_BLACKBOX 0
+#define TBLR_SKETCH_TAGGED   1
+
 /* Problem statement: geometry and tessellation, admissibility, rank
  * (Algorithm 2 "Require": a b x b tessellation of a d-dimensional geometry,
  * target rank k; §2.4 oversampling p; §5.3 extra tag columns e). */
@@ -78,7 +89,7 @@ typedef struct {
     int32_t e;          /* extra tag columns, >= 0 (the paper uses 3) */
     int32_t precision;  /* TBLR_FP64 or TBLR_MIXED */
     int32_t nearfield;  /* TBLR_NEARFIELD_PROBE or TBLR_NEARFIELD_EXACT */
-    int32_t reserved;
+    int32_t sketch;     /* TBLR_SKETCH_BLACKBOX or TBLR_SKETCH_TAGGED (tblr_compress) */
 } tblr_problem;
 
 /* Sizes that follow from a problem (no device work). */
@@ -181,6 +192,17 @@ size_t tblr_sketch_workspace(const tblr_problem *prob);
 int tblr_sketch(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
                 const double *omega_psi, double *yz, void *ws, size_t ws_bytes, void *stream);
 
+/* Tag-factored samples (see TBLR_SKETCH_TAGGED): S(I_i, :) = sum_c tau[i, c]
+ * A_ic G_c and R(I_i, :) = sum_c tau[i, c] (A^T)_ic H_c directly from the
+ * projected tags tau (b x b, from tblr_decode) and G, H ([n*r], original point
+ * order).  s, rr: [n*r] box-major.  FP64, or with TBLR_MIXED on the tensor
+ * cores (split FP16, FP32 accumulation, FP32 tags).  The sketch Y, Z is never
+ * formed.  ws: tblr_tagged_sketch_workspace bytes. */
+size_t tblr_tagged_sketch_workspace(const tblr_problem *prob);
+int tblr_tagged_sketch(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
+                       const double *tau, const double *G, const double *H, double *s,
+                       double *rr, void *ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------ a4: tag decode (§4.1, §5.1, §5.3)
  * z_i = unit vector of null(T(N_i, :)) nearest to 1/sqrt(ell) (the normalised
  * projection of the all-ones direction; eq. tagsubmat), tau_i = T z_i (projected
@@ -230,7 +252,8 @@ int tblr_nearfield(const tblr_problem *prob, const tblr_layout *lay, const doubl
 /* ------------------------------------------- whole pipeline (Table 1)
  * Runs a2..a8 on a tessellated problem (tblr_tessellate and
  * tblr_nearfield_offsets already enqueued; m_max is their host-read value).
- * Outputs as in the step calls: yz [n*2C] (kept for inspection), z, tau, rho,
+ * Outputs as in the step calls: yz [n*2C] (kept for inspection; unused and
+ * may be NULL with TBLR_SKETCH_TAGGED), z, tau, rho,
  * u, v [n*k], ranks [b], at [b*b*k*k], bnear [nf_off[b*S3]].  Scratch (Omega,
  * S, R and the steps' workspaces) comes from ws, tblr_compress_workspace bytes. */
 size_t tblr_compress_workspace(const tblr_problem *prob, int32_t m_max);
@@ -267,6 +290,85 @@ int tblr_release_device_cache(void);
  * call synchronises the device, stores the counter in *count, resets it, and
  * returns TBLR_OK (or TBLR_ECUDA). */
 int tblr_device_timeouts(unsigned int *count /* host */);
+
+/* ------------------------------------------------------- batched jobs
+ * Independent compressions with uneven sizes, box sizes, ranks and
+ * dimensions run together: every job's pipeline is enqueued on one of
+ * n_streams worker streams (largest estimated sketch work first, to the least
+ * loaded stream), forked from and joined back into `stream` with events, with
+ * no host synchronisation, so the batch can be captured into one CUDA graph.
+ * A job's buffers are caller-owned device memory sized as for the step calls;
+ * ws must hold max(tblr_tessellate_workspace, tblr_compress_workspace(m_max)).
+ * tblr_batch_plan tessellates each job once (synchronising `stream`) and fills
+ * m_max and nf_total; tblr_batch_run then requires the same points (the
+ * near-field sizes depend on them). */
+typedef struct {
+    tblr_problem prob;
+    const double *points, *T, *G, *H, *dense;   /* inputs (dense: TBLR_KERNEL_DENSE only) */
+    tblr_layout lay;                             /* tessellation outputs */
+    int64_t *nf_off;                             /* [b*S3 + 1] */
+    int32_t *m_max_dev;                          /* [1] */
+    int32_t m_max;                               /* filled by tblr_batch_plan */
+    int32_t reserved;
+    int64_t nf_total;                            /* filled by tblr_batch_plan */
+    double *yz, *z, *tau, *rho, *u, *v;          /* outputs as in tblr_compress */
+    int32_t *ranks;
+    double *at, *bnear;
+    void *ws;
+    size_t ws_bytes;
+} tblr_job;
+
+int tblr_batch_plan(int n_jobs, tblr_job *jobs, void *stream);
+int tblr_batch_run(int n_jobs, const tblr_job *jobs, int n_streams, void *stream);
+
+/* A captured batch: tblr_graph_create records tblr_batch_run on `stream`
+ * (which must not be the legacy default stream) into a CUDA graph;
+ * tblr_graph_launch replays the whole batch with one launch. */
+typedef struct tblr_graph tblr_graph;
+int tblr_graph_create(int n_jobs, const tblr_job *jobs, int n_streams, void *stream,
+                      tblr_graph **out);
+int tblr_graph_launch(tblr_graph *graph, void *stream);
+void tblr_graph_destroy(tblr_graph *graph);
+
+/* ------------------------------------------------------------ serving
+ * A continuous-batching server.  Requests queue in arrival order; a request
+ * is admitted when one of max_inflight stream slots is free and its
+ * first-phase device memory (inputs, tessellation) fits in mem_budget_bytes;
+ * its second phase (the pipeline and outputs), sized exactly after
+ * tessellation, starts when that memory fits too (a request that alone
+ * exceeds the budget runs when nothing else compresses).  Admitted requests
+ * run on their own streams and overlap on the device; results do not depend
+ * on what runs beside them.  Inputs and outputs are host buffers owned by the
+ * caller and must stay valid until tblr_server_wait returns (pinned memory
+ * makes the copies asynchronous).  Output sizes are those of
+ * tblr_compress_host; a request whose near field exceeds bnear_capacity
+ * finishes with status TBLR_EWORKSPACE.  Kernel operators only. */
+typedef struct {
+    tblr_problem prob;
+    const double *points_h, *T_h, *G_h, *H_h;
+    int32_t *perm_h, *offsets_h, *nbr_h, *ranks_h;
+    double *u_h, *v_h, *at_h, *bnear_h;
+    int64_t bnear_capacity;
+} tblr_request;
+
+typedef struct {
+    uint64_t completed, failed, pending, active;
+    double p50_ms, p99_ms;      /* submit-to-done latency of completed requests */
+    double throughput;          /* completed / (last completion - first submit), per second */
+    size_t mem_in_use, mem_peak;
+} tblr_server_report;
+
+typedef struct tblr_server tblr_server;
+int tblr_server_create(tblr_server **out, int device, size_t mem_budget_bytes, int max_inflight);
+int tblr_server_submit(tblr_server *server, const tblr_request *req, uint64_t *ticket);
+/* Waits up to timeout_ms for a request; TBLR_ETIMEOUT if it is not done yet
+ * (the request keeps running; wait again).  *status is the request's own
+ * result status.  The ticket is released when this returns TBLR_OK. */
+int tblr_server_wait(tblr_server *server, uint64_t ticket, int timeout_ms, int *status,
+                     double *latency_ms);
+int tblr_server_stats(tblr_server *server, tblr_server_report *out);
+/* Finishes every queued and running request, then frees the server. */
+void tblr_server_destroy(tblr_server *server);
 
 #ifdef __cplusplus
 }

@@ -15,11 +15,12 @@ struct WsPlan {
 
 WsPlan plan_workspace(const Prob &P, const tblr_problem *prob, int32_t m_max) {
   WsPlan w;
-  w.omega = align256(sizeof(double) * 2 * P.C * P.n);
+  const bool tagged = prob->sketch == TBLR_SKETCH_TAGGED;
+  w.omega = tagged ? 0 : align256(sizeof(double) * 2 * P.C * P.n);
   w.s = align256(sizeof(double) * P.n * P.r);
   w.r = w.s;
   w.col = align256(tblr_col_workspace(prob));
-  w.sketch = align256(tblr_sketch_workspace(prob));
+  w.sketch = align256(tagged ? tblr_tagged_sketch_workspace(prob) : tblr_sketch_workspace(prob));
   w.nf = align256(tblr_nearfield_workspace(prob, m_max));
   w.total = w.omega + w.s + w.r + w.col + w.sketch + w.nf;
   return w;
@@ -41,7 +42,9 @@ extern "C" int tblr_compress(const tblr_problem *prob, const tblr_layout *lay, c
   Prob P;
   TBLR_TRY(check_problem(prob, &P));
   TBLR_TRY(check_layout(P, lay));
-  TBLR_REQUIRE(T && G && H && yz && z && tau && rho && u && v && ranks && at && nf_off && bnear,
+  const bool tagged = prob->sketch == TBLR_SKETCH_TAGGED;
+  TBLR_REQUIRE(T && G && H && (yz || tagged) && z && tau && rho && u && v && ranks && at &&
+                   nf_off && bnear,
                "every input and output pointer must be non-NULL");
   const WsPlan w = plan_workspace(P, prob, m_max);
   TBLR_REQUIRE(ws != nullptr && ws_bytes >= w.total, "compress workspace too small (%zu < %zu)",
@@ -53,11 +56,17 @@ extern "C" int tblr_compress(const tblr_problem *prob, const tblr_layout *lay, c
   char *colws = base + w.omega + w.s + w.r;
   char *skws = colws + w.col;
   char *nfws = skws + w.sketch;
-  // Step I (Algorithm 2): test matrices, sketch, decode, combine, col.
-  TBLR_TRY(tblr_test_matrices(prob, lay, T, G, H, omega, stream));
-  TBLR_TRY(tblr_sketch(prob, lay, dense, omega, yz, skws, w.sketch, stream));
-  TBLR_TRY(tblr_decode(prob, lay, T, z, tau, rho, stream));
-  TBLR_TRY(tblr_combine(prob, lay, yz, z, S, R, stream));
+  // Step I (Algorithm 2): test matrices, sketch, decode, combine, col.  The
+  // tag-factored sketch decodes first and forms S and R without Y and Z.
+  if (tagged) {
+    TBLR_TRY(tblr_decode(prob, lay, T, z, tau, rho, stream));
+    TBLR_TRY(tblr_tagged_sketch(prob, lay, dense, tau, G, H, S, R, skws, w.sketch, stream));
+  } else {
+    TBLR_TRY(tblr_test_matrices(prob, lay, T, G, H, omega, stream));
+    TBLR_TRY(tblr_sketch(prob, lay, dense, omega, yz, skws, w.sketch, stream));
+    TBLR_TRY(tblr_decode(prob, lay, T, z, tau, rho, stream));
+    TBLR_TRY(tblr_combine(prob, lay, yz, z, S, R, stream));
+  }
   TBLR_TRY(tblr_col(prob, lay, S, u, ranks, colws, w.col, stream));
   TBLR_TRY(tblr_col(prob, lay, R, v, ranks, colws, w.col, stream));
   // Step II (Table 1): Atilde = U^T (A V).

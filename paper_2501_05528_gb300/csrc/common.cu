@@ -37,6 +37,8 @@ int check_problem(const tblr_problem *in, Prob *P) {
   TBLR_REQUIRE(in->precision == TBLR_FP64 || in->precision == TBLR_MIXED, "bad precision");
   TBLR_REQUIRE(in->nearfield == TBLR_NEARFIELD_PROBE || in->nearfield == TBLR_NEARFIELD_EXACT,
                "bad nearfield mode");
+  TBLR_REQUIRE(in->sketch == TBLR_SKETCH_BLACKBOX || in->sketch == TBLR_SKETCH_TAGGED,
+               "bad sketch mode");
   P->d = in->d;
   P->kernel = in->kernel;
   P->n = in->n;

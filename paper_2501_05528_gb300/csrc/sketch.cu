@@ -6,6 +6,8 @@
 // 256 * CPT columns; each K step generates the BM x BK tile of A once (a log
 // or rsqrt costs ~36 DFMA) and contracts it with the BK x (256 CPT) slice of X
 // staged in shared memory, so every generated entry feeds up to 1280 DFMAs.
+#include <algorithm>
+
 #include "common.cuh"
 #include "mixed.cuh"
 
@@ -58,10 +60,20 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Two-stage pipeline: while the FP64 pipe contracts stage `cur`, the X slice of
 // the next K step streams into the other stage with cp.async and the next
 // kernel tile is generated.
-template <class Op, int CPT>
+// Tag factoring (TAGGED): entry (p, q) is scaled by tau[box_of[p] * b + box_of[q]], and
+// output columns c >= split go to y2[p * ldy2 + c - split].
+struct TagArgs {
+  const double *tau;
+  const int32_t *box_of;
+  int b;
+  int64_t split, ldy2;
+  double *y2;
+};
+
+template <class Op, int CPT, bool TAGGED>
 __global__ void __launch_bounds__(kThreads, 1)
     apply_fp64_kernel(Op op, const double *__restrict__ xt, int64_t n, int64_t ncols,
-                      double *__restrict__ y, int64_t ldy) {
+                      double *__restrict__ y, int64_t ldy, TagArgs tg) {
   extern __shared__ double sm[];
   constexpr int NT = kThreads * CPT;
   double *As = sm;                   // [2][kBK][kBM]
@@ -92,7 +104,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int r = tid % kBM, kk = tid / kBM;
       const int64_t gi = row0 + r, gj = k0 + kk;
       double v = 0.0;
-      if (gi < n && gj < n) v = op(gi, gj);
+      if (gi < n && gj < n) {
+        v = op(gi, gj);
+        if (TAGGED) v *= tg.tau[(int64_t)tg.box_of[gi] * tg.b + tg.box_of[gj]];
+      }
       As[buf * kBK * kBM + kk * kBM + r] = v;
     }
   };
@@ -140,31 +155,49 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int r = 0; r < kBM; ++r) {
       const int64_t gi = row0 + r;
-      if (gi < n) y[gi * ldy + c] = acc[r][s];
+      if (gi < n) {
+        if (!TAGGED || c < tg.split)
+          y[gi * ldy + c] = acc[r][s];
+        else
+          tg.y2[gi * tg.ldy2 + (c - tg.split)] = acc[r][s];
+      }
     }
   }
 }
 
-template <class Op, int CPT>
+template <class Op, int CPT, bool TAGGED>
 int launch_apply_fp64_cpt(const Op &op, const double *xt, int64_t n, int64_t ncols, double *y,
-                          int64_t ldy, cudaStream_t s) {
+                          int64_t ldy, const TagArgs &tg, cudaStream_t s) {
   const size_t smem = sizeof(double) * 2 * (kBK * kBM + kBK * kThreads * CPT);
-  auto kern = apply_fp64_kernel<Op, CPT>;
+  auto kern = apply_fp64_kernel<Op, CPT, TAGGED>;
   TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((unsigned)cdiv(n, kBM), (unsigned)cdiv(ncols, kThreads * CPT));
-  kern<<<grid, kThreads, smem, s>>>(op, xt, n, ncols, y, ldy);
+  kern<<<grid, kThreads, smem, s>>>(op, xt, n, ncols, y, ldy, tg);
   return launch_status("apply_fp64_kernel");
 }
 
-template <class Op>
+template <class Op, bool TAGGED = false>
 int launch_apply_fp64(const Op &op, const double *xt, int64_t n, int64_t ncols, double *y,
-                      int64_t ldy, cudaStream_t s) {
+                      int64_t ldy, cudaStream_t s, const TagArgs &tg = TagArgs{}) {
   const int64_t cpt = cdiv(ncols, kThreads);
-  if (cpt <= 1) return launch_apply_fp64_cpt<Op, 1>(op, xt, n, ncols, y, ldy, s);
-  if (cpt <= 2) return launch_apply_fp64_cpt<Op, 2>(op, xt, n, ncols, y, ldy, s);
-  if (cpt <= 3) return launch_apply_fp64_cpt<Op, 3>(op, xt, n, ncols, y, ldy, s);
-  if (cpt <= 4) return launch_apply_fp64_cpt<Op, 4>(op, xt, n, ncols, y, ldy, s);
-  return launch_apply_fp64_cpt<Op, 5>(op, xt, n, ncols, y, ldy, s);
+  if (cpt <= 1) return launch_apply_fp64_cpt<Op, 1, TAGGED>(op, xt, n, ncols, y, ldy, tg, s);
+  if (cpt <= 2) return launch_apply_fp64_cpt<Op, 2, TAGGED>(op, xt, n, ncols, y, ldy, tg, s);
+  if (cpt <= 3) return launch_apply_fp64_cpt<Op, 3, TAGGED>(op, xt, n, ncols, y, ldy, tg, s);
+  if (cpt <= 4) return launch_apply_fp64_cpt<Op, 4, TAGGED>(op, xt, n, ncols, y, ldy, tg, s);
+  return launch_apply_fp64_cpt<Op, 5, TAGGED>(op, xt, n, ncols, y, ldy, tg, s);
+}
+
+// [G | H] in box-major order, K-major: out[c * n + p] (c < r from G, else H).
+__global__ void gather_gh_kernel(const double *__restrict__ G, const double *__restrict__ H,
+                                 const int32_t *__restrict__ perm, int64_t n, int r, int sides,
+                                 double *__restrict__ out) {
+  const int64_t total = n * r * sides;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / n, p = i % n;
+    const int64_t src = (int64_t)perm[p] * r + (c < r ? c : c - r);
+    out[i] = (c < r) ? G[src] : H[src];
+  }
 }
 
 }  // namespace
@@ -247,4 +280,48 @@ extern "C" int tblr_sketch(const tblr_problem *prob, const tblr_layout *lay, con
   TBLR_TRY(apply_any(P, lay, dense, omega_psi, C, yz, 2 * C, 0, TBLR_FP64, ws, ws_bytes, s));
   return apply_any(P, lay, dense, omega_psi + C * P.n, C, yz + C, 2 * C, 1, TBLR_FP64, ws, ws_bytes,
                    s);
+}
+
+extern "C" size_t tblr_tagged_sketch_workspace(const tblr_problem *prob) {
+  Prob P;
+  if (check_problem(prob, &P) != TBLR_OK) return 0;
+  if (P.precision == TBLR_MIXED && symmetric_kernel(P.kernel)) return tagged_mixed_workspace(P);
+  return align256(sizeof(double) * 2 * P.r * P.n);
+}
+
+extern "C" int tblr_tagged_sketch(const tblr_problem *prob, const tblr_layout *lay,
+                                  const double *dense, const double *tau, const double *G,
+                                  const double *H, double *s_out, double *r_out, void *ws,
+                                  size_t ws_bytes, void *stream) {
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_TRY(check_layout(P, lay));
+  TBLR_REQUIRE(tau && G && H && s_out && r_out, "tau, G, H, s and rr must be non-NULL");
+  TBLR_REQUIRE(ws != nullptr && ws_bytes >= tblr_tagged_sketch_workspace(prob),
+               "tagged sketch workspace too small");
+  cudaStream_t s = as_stream(stream);
+  if (P.precision == TBLR_MIXED) {
+    TBLR_REQUIRE(symmetric_kernel(P.kernel), "mixed precision needs a built-in kernel operator");
+    return tagged_sketch_mixed(P, lay, tau, G, H, s_out, r_out, ws, ws_bytes, s);
+  }
+  double *x = static_cast<double *>(ws);
+  const bool sym = symmetric_kernel(P.kernel);
+  gather_gh_kernel<<<(unsigned)std::min<int64_t>(cdiv(2 * P.r * P.n, 256), 152 * 32), 256, 0, s>>>(
+      G, H, lay->perm, P.n, P.r, 2, x);
+  TBLR_TRY(launch_status("gather_gh_kernel"));
+  TagArgs tg{tau, lay->box_of, (int)P.b, P.r, P.r, r_out};
+  if (sym) {
+    // S | R = A' [G | H] with A'(p, q) = tau[box p][box q] A(p, q), one pass over A.
+    return with_operator(P, lay, dense, 0, [&](auto op) {
+      return launch_apply_fp64<decltype(op), true>(op, x, P.n, 2 * P.r, s_out, P.r, s, tg);
+    });
+  }
+  TagArgs only{tau, lay->box_of, (int)P.b, P.r, P.r, nullptr};
+  TBLR_TRY(with_operator(P, lay, dense, 0, [&](auto op) {
+    return launch_apply_fp64<decltype(op), true>(op, x, P.n, P.r, s_out, P.r, s, only);
+  }));
+  // R_i = sum_c tau_ic (A^T)_ic H_c
+  return with_operator(P, lay, dense, 1, [&](auto op) {
+    return launch_apply_fp64<decltype(op), true>(op, x + P.r * P.n, P.n, P.r, r_out, P.r, s, only);
+  });
 }

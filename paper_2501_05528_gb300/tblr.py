@@ -19,6 +19,7 @@ TBLR_OK, TBLR_EINVAL, TBLR_ECUDA, TBLR_EUNSUPPORTED, TBLR_EWORKSPACE, TBLR_ETIME
 KERNELS = {"laplace2d": 1, "laplace3d": 2, "dense": 3}
 FP64, MIXED = 0, 1
 NEARFIELD_PROBE, NEARFIELD_EXACT = 0, 1
+SKETCH_BLACKBOX, SKETCH_TAGGED = 0, 1
 
 
 class TblrError(RuntimeError):
@@ -33,7 +34,7 @@ class Problem(ctypes.Structure):
                 ("grid", ctypes.c_int32 * 3), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("k", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("e", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("nearfield", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("nearfield", ctypes.c_int32), ("sketch", ctypes.c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -45,6 +46,29 @@ class Sizes(ctypes.Structure):
 class LayoutStruct(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in
                 ("perm", "box_of", "offsets", "nbr", "nnbr", "colour", "pts")]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("prob", Problem)] + [(n, ctypes.c_void_p) for n in
+                                      ("points", "T", "G", "H", "dense")] + [
+        ("lay", LayoutStruct), ("nf_off", ctypes.c_void_p), ("m_max_dev", ctypes.c_void_p),
+        ("m_max", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nf_total", ctypes.c_int64)] + [
+        (n, ctypes.c_void_p) for n in ("yz", "z", "tau", "rho", "u", "v", "ranks", "at", "bnear",
+                                       "ws")] + [("ws_bytes", ctypes.c_size_t)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("prob", Problem)] + [(n, ctypes.c_void_p) for n in (
+        "points_h", "T_h", "G_h", "H_h", "perm_h", "offsets_h", "nbr_h", "ranks_h", "u_h", "v_h",
+        "at_h", "bnear_h")] + [("bnear_capacity", ctypes.c_int64)]
+
+
+class ServerReport(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("active", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("throughput", ctypes.c_double), ("mem_in_use", ctypes.c_size_t),
+                ("mem_peak", ctypes.c_size_t)]
 
 
 _VP, _I64, _SZ, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t, ctypes.c_int32
@@ -65,6 +89,8 @@ _SIGNATURES = {
     "tblr_sketch_workspace": (_SZ, [_PP]),
     "tblr_sketch": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "tblr_decode": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP]),
+    "tblr_tagged_sketch_workspace": (_SZ, [_PP]),
+    "tblr_tagged_sketch": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "tblr_combine": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP]),
     "tblr_col_workspace": (_SZ, [_PP]),
     "tblr_col": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _SZ, _VP]),
@@ -79,6 +105,20 @@ _SIGNATURES = {
                                           _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
     "tblr_release_device_cache": (ctypes.c_int, []),
     "tblr_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
+    "tblr_batch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Job), _VP]),
+    "tblr_batch_run": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Job), ctypes.c_int, _VP]),
+    "tblr_graph_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Job), ctypes.c_int, _VP,
+                                         ctypes.POINTER(_VP)]),
+    "tblr_graph_launch": (ctypes.c_int, [_VP, _VP]),
+    "tblr_graph_destroy": (None, [_VP]),
+    "tblr_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _SZ, ctypes.c_int]),
+    "tblr_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(Request),
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "tblr_server_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "tblr_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ServerReport)]),
+    "tblr_server_destroy": (None, [_VP]),
 }
 
 _lib = None
@@ -123,13 +163,13 @@ def _dev():
 
 
 def make_problem(d, kernel, n, grid, lo, hi, k, p=10, e=3, precision=FP64,
-                 nearfield=NEARFIELD_PROBE) -> Problem:
+                 nearfield=NEARFIELD_PROBE, sketch=SKETCH_BLACKBOX) -> Problem:
     g = list(grid) + [1] * (3 - len(grid))
     lo3 = list(lo) + [0.0] * (3 - len(lo))
     hi3 = list(hi) + [1.0] * (3 - len(hi))
     kind = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     return Problem(d, kind, n, (ctypes.c_int32 * 3)(*g), (ctypes.c_double * 3)(*lo3),
-                   (ctypes.c_double * 3)(*hi3), k, p, e, precision, nearfield, 0)
+                   (ctypes.c_double * 3)(*hi3), k, p, e, precision, nearfield, sketch)
 
 
 def tblr_sizes_of(prob: Problem) -> Sizes:
@@ -230,6 +270,18 @@ def tblr_decode(prob, lay, T):
     _check(lib().tblr_decode(ctypes.byref(prob), lay.ref, _p(T), _p(z), _p(tau), _p(rho),
                              _stream()), "tblr_decode")
     return z, tau, rho
+
+
+def tblr_tagged_sketch(prob, lay, tau, G, H, dense=None):
+    """S, R from the projected tags (TBLR_SKETCH_TAGGED), without forming Y, Z."""
+    sz = tblr_sizes_of(prob)
+    s = torch.empty(prob.n, sz.r, dtype=torch.float64, device=_dev())
+    rr = torch.empty_like(s)
+    nbytes = lib().tblr_tagged_sketch_workspace(ctypes.byref(prob))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=_dev())
+    _check(lib().tblr_tagged_sketch(ctypes.byref(prob), lay.ref, _p(dense), _p(tau), _p(G), _p(H),
+                                    _p(s), _p(rr), _p(ws), nbytes, _stream()), "tblr_tagged_sketch")
+    return s, rr
 
 
 def tblr_combine(prob, lay, yz, z):
@@ -355,3 +407,150 @@ def tblr_compress_host(prob, points, T, G, H, dense=None, outputs=None, stream=N
     _check(status, "tblr_compress_host")
     o["bnear_size"] = need.value
     return o
+
+
+# ------------------------------------------------------------------ batches
+
+class BatchJob:
+    """Device buffers of one job of a batch and its C descriptor (tblr_job)."""
+
+    def __init__(self, prob, points, T, G, H):
+        self.prob = prob
+        self.points, self.T, self.G, self.H = (x.contiguous() for x in (points, T, G, H))
+        sz = tblr_sizes_of(prob)
+        dev = _dev()
+        self.sz = sz
+        self.lay = Layout(prob)
+        self.nf_off = torch.empty(sz.b * sz.s3 + 1, dtype=torch.int64, device=dev)
+        self.m_max_dev = torch.empty(1, dtype=torch.int32, device=dev)
+        tws = lib().tblr_tessellate_workspace(ctypes.byref(prob))
+        self.ws = torch.empty(max(tws, 1), dtype=torch.uint8, device=dev)
+        self.c = Job(prob=prob, points=self.points.data_ptr(), T=self.T.data_ptr(),
+                     G=self.G.data_ptr(), H=self.H.data_ptr(), dense=None, lay=self.lay.struct,
+                     nf_off=self.nf_off.data_ptr(), m_max_dev=self.m_max_dev.data_ptr(),
+                     ws=self.ws.data_ptr(), ws_bytes=self.ws.numel())
+
+    def allocate_outputs(self):
+        """After tblr_batch_plan: outputs and the full workspace, sized from the plan."""
+        sz, dev, n, k = self.sz, _dev(), self.prob.n, self.prob.k
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.out = Compressed(
+            yz=torch.empty(n, sz.sketch_cols, **f64), z=torch.empty(sz.b, sz.ell, **f64),
+            tau=torch.empty(sz.b, sz.b, **f64), rho=torch.empty(sz.b, **f64),
+            u=torch.empty(n, k, **f64), v=torch.empty(n, k, **f64),
+            ranks=torch.empty(sz.b, dtype=torch.int32, device=dev),
+            at=torch.empty(sz.b, sz.b, k, k, **f64),
+            bnear=torch.empty(max(self.c.nf_total, 1), **f64),
+            nf_off=self.nf_off, m_max=self.c.m_max, total=self.c.nf_total, layout=self.lay)
+        need = max(lib().tblr_compress_workspace(ctypes.byref(self.prob), self.c.m_max),
+                   self.ws.numel())
+        self.ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        o = self.out
+        for name in ("yz", "z", "tau", "rho", "u", "v", "ranks", "at", "bnear"):
+            setattr(self.c, name, getattr(o, name).data_ptr())
+        self.c.ws = self.ws.data_ptr()
+        self.c.ws_bytes = self.ws.numel()
+
+
+def _job_array(jobs):
+    arr = (Job * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i] = j.c
+    return arr
+
+
+def tblr_batch_plan(jobs):
+    _require_cuda()
+    arr = _job_array(jobs)
+    _check(lib().tblr_batch_plan(len(jobs), arr, _stream()), "tblr_batch_plan")
+    for i, j in enumerate(jobs):
+        j.c.m_max, j.c.nf_total = arr[i].m_max, arr[i].nf_total
+        j.allocate_outputs()
+
+
+def tblr_batch_run(jobs, n_streams=4):
+    arr = _job_array(jobs)
+    _check(lib().tblr_batch_run(len(jobs), arr, n_streams, _stream()), "tblr_batch_run")
+
+
+class Graph:
+    """A batch captured into one CUDA graph (tblr_graph_create / launch / destroy)."""
+
+    def __init__(self, jobs, n_streams=4):
+        self._jobs = jobs
+        self.h = ctypes.c_void_p()
+        arr = _job_array(jobs)
+        _check(lib().tblr_graph_create(len(jobs), arr, n_streams, _stream(), ctypes.byref(self.h)),
+               "tblr_graph_create")
+
+    def launch(self):
+        _check(lib().tblr_graph_launch(self.h, _stream()), "tblr_graph_launch")
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().tblr_graph_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+
+# ------------------------------------------------------------------ serving
+
+class Server:
+    """Continuous-batching server (tblr_server_*).  submit() takes pinned host arrays."""
+
+    def __init__(self, mem_budget_bytes, max_inflight=8, device=None):
+        _require_cuda()
+        self.h = ctypes.c_void_p()
+        dev = torch.cuda.current_device() if device is None else device
+        _check(lib().tblr_server_create(ctypes.byref(self.h), dev, int(mem_budget_bytes),
+                                        max_inflight), "tblr_server_create")
+        self._keep = {}
+
+    def submit(self, prob, points, T, G, H, outputs):
+        """points/T/G/H and outputs (dict as from host_outputs) are CPU tensors, pinned."""
+        o = outputs
+        req = Request(prob=prob, points_h=points.data_ptr(), T_h=T.data_ptr(), G_h=G.data_ptr(),
+                      H_h=H.data_ptr(), perm_h=o["perm"].data_ptr(),
+                      offsets_h=o["offsets"].data_ptr(), nbr_h=o["nbr"].data_ptr(),
+                      ranks_h=o["ranks"].data_ptr(), u_h=o["u"].data_ptr(), v_h=o["v"].data_ptr(),
+                      at_h=o["at"].data_ptr(), bnear_h=o["bnear"].data_ptr(),
+                      bnear_capacity=o["bnear"].numel())
+        ticket = ctypes.c_uint64()
+        _check(lib().tblr_server_submit(self.h, ctypes.byref(req), ctypes.byref(ticket)),
+               "tblr_server_submit")
+        self._keep[ticket.value] = (points, T, G, H, outputs)
+        return ticket.value
+
+    def wait(self, ticket, timeout_ms=600000):
+        st, lat = ctypes.c_int(), ctypes.c_double()
+        _check(lib().tblr_server_wait(self.h, ticket, timeout_ms, ctypes.byref(st),
+                                      ctypes.byref(lat)), "tblr_server_wait")
+        self._keep.pop(ticket, None)
+        return st.value, lat.value
+
+    def stats(self):
+        r = ServerReport()
+        _check(lib().tblr_server_stats(self.h, ctypes.byref(r)), "tblr_server_stats")
+        return {f: getattr(r, f) for f, _ in ServerReport._fields_}
+
+    def close(self):
+        if self.h.value:
+            lib().tblr_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        self.close()
+
+
+def host_outputs(prob, bnear_capacity, pin=True):
+    """Host output buffers for one request (sizes as in tblr_compress_host)."""
+    sz = tblr_sizes_of(prob)
+    n, b, k = prob.n, sz.b, prob.k
+
+    def e(*shape, dtype):
+        t = torch.empty(*shape, dtype=dtype)
+        return t.pin_memory() if pin else t
+    return dict(perm=e(n, dtype=torch.int32), offsets=e(b + 1, dtype=torch.int32),
+                nbr=e(b * sz.s3, dtype=torch.int32), ranks=e(b, dtype=torch.int32),
+                u=e(n, k, dtype=torch.float64), v=e(n, k, dtype=torch.float64),
+                at=e(b, b, k, k, dtype=torch.float64),
+                bnear=e(max(int(bnear_capacity), 1), dtype=torch.float64))

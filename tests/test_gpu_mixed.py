@@ -56,9 +56,11 @@ def test_mixed_apply_matches_fp64_oracle(kind, d, grid, n, ncols):
     assert row_err.max() < 10 * MIXED_BOUND
 
 
+@pytest.mark.parametrize("sketch", [0, 1], ids=["blackbox", "tagged"])
 @pytest.mark.parametrize("kind,d,grid,n,k,e", [("laplace2d", 2, (6, 6), 3001, 8, 3),
-                                              ("laplace3d", 3, (4, 4, 4), 2501, 6, 1)])
-def test_mixed_compression_within_bound(kind, d, grid, n, k, e):
+                                              ("laplace3d", 3, (4, 4, 4), 2501, 6, 1),
+                                              ("laplace3d", 3, (5, 5, 5), 6001, 12, 3)])
+def test_mixed_compression_within_bound(kind, d, grid, n, k, e, sketch):
     tb = _tb()
     pts = inputs.uniform_points(n, d, seed=7 * n)
     b = int(np.prod(grid))
@@ -66,7 +68,7 @@ def test_mixed_compression_within_bound(kind, d, grid, n, k, e):
     T, G, H = inputs.tagging_draws(b, ell, n, k + 10, seed=7 * n + 1)
     lo, hi = (0.0,) * d, (1.0,) * d
     ref = orc.reconstruct_tag(pts, grid, lo, hi, kind, T, G, H, k, 10)
-    prob = tb.make_problem(d, kind, n, grid, lo, hi, k, 10, e, precision=tb.MIXED)
+    prob = tb.make_problem(d, kind, n, grid, lo, hi, k, 10, e, precision=tb.MIXED, sketch=sketch)
     dev = torch.device("cuda")
     t = lambda a: torch.as_tensor(a, device=dev)
     out = tb.compress(prob, t(pts), t(T), t(G), t(H))
@@ -79,5 +81,5 @@ def test_mixed_compression_within_bound(kind, d, grid, n, k, e):
     rep = dict(U=out.u.cpu().numpy(), V=out.v.cpu().numpy(), At=out.at.cpu().numpy(), B=B)
     rep_o = dict(U=ref["U"], V=ref["V"], At=ref["coupling"], B=ref["nearfield"])
     err = metrics.ublr_difference(off, nbr, cnt, s3, ref["ranks"], rep, rep_o)
-    print(f"mixed compression {kind}: rel err vs FP64 oracle {err:.3e}")
+    print(f"mixed compression {kind} n={n} sketch={sketch}: rel err vs FP64 oracle {err:.3e}")
     assert err < MIXED_BOUND

@@ -217,3 +217,37 @@ def test_host_buffer_entry_point_matches(case):
     assert np.array_equal(o["u"].numpy(), g["u"])
     assert np.array_equal(o["at"].numpy(), g["at"])
     assert np.array_equal(o["bnear"].numpy()[:o["bnear_size"]], g["bnear"])
+
+
+def test_tagged_sketch_matches_the_black_box_samples(case):
+    """TBLR_SKETCH_TAGGED forms S = sum_c tau_c A_ic G_c directly; it must equal the oracle's
+    S = sum_j z_j Y_j (eq. extend_test_mat), and the tagged pipeline its reconstruction."""
+    tb = _tb()
+    c, x, res, g = case["c"], case["x"], case["res"], case["gpu"]
+    d, grid, k = c["d"], c["grid"], c["k"]
+    n = case["n"]
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    prob = tb.make_problem(d, x["kind"], n, grid, x["lo"], x["hi"], k, 10, c["e"],
+                           sketch=tb.SKETCH_TAGGED)
+    pts, T, G, H = t(x["pts"]), t(x["T"]), t(x["G"]), t(x["H"])
+    dense = None if x["dense"] is None else t(x["dense"])
+    lay = tb.tblr_tessellate(prob, pts)
+    z, tau, rho = tb.tblr_decode(prob, lay, T)
+    s, rr = tb.tblr_tagged_sketch(prob, lay, tau, G, H, dense=dense)
+    full = tb.tblr_compress(prob, lay, T, G, H, dense=dense)
+    torch.cuda.synchronize()
+    yz = np.hstack([res["Y"], res["Z"]])
+    scale = np.linalg.norm(yz) * max(1.0, np.abs(res["z"]).max())
+    assert np.linalg.norm(s.cpu().numpy() - res["S"]) <= 1e-12 * scale
+    assert np.linalg.norm(rr.cpu().numpy() - res["R"]) <= 1e-12 * scale
+    tess = res["tess"]
+    s3 = 3 ** d
+    off = tess["offsets"]
+    nbr, cnt = metrics.padded_neighbours(tess["nbrs"], s3)
+    B = metrics.blocks_from_flat(full.bnear.cpu().numpy(), full.nf_off.cpu().numpy(), nbr, cnt,
+                                 off, s3)
+    rep = dict(U=full.u.cpu().numpy(), V=full.v.cpu().numpy(), At=full.at.cpu().numpy(), B=B)
+    rep_o = dict(U=res["U"], V=res["V"], At=res["coupling"], B=res["nearfield"])
+    err = metrics.ublr_difference(off, nbr, cnt, s3, res["ranks"], rep, rep_o)
+    assert err <= 1e-10, err
