@@ -207,8 +207,10 @@ class Runner:
         t = lambda a: torch.as_tensor(a, device=dev)
         self.pts, self.T, self.G, self.H = t(pts), t(T), t(G), t(H)
         d = w["d"]
+        self.tagged = w.get("sketch", 0) == 1
         self.prob = tb.make_problem(d, w["kernel"], w["n"], w["grid"], (0.0,) * d, (1.0,) * d,
-                                    w["k"], w["p"], w["e"], precision=w.get("precision", 0))
+                                    w["k"], w["p"], w["e"], precision=w.get("precision", 0),
+                                    sketch=w.get("sketch", 0))
         self.sz = tb.tblr_sizes_of(self.prob)
         lay = tb.tblr_tessellate(self.prob, self.pts)
         nf_off, m_max = tb.tblr_nearfield_offsets(self.prob, lay)
@@ -227,15 +229,22 @@ class Runner:
                                dtype=torch.uint8, device=dev)
         self.colws = torch.empty(tb.lib().tblr_col_workspace(tb.ctypes.byref(self.prob)),
                                  dtype=torch.uint8, device=dev)
-        self.skws = torch.empty(max(1, tb.lib().tblr_sketch_workspace(tb.ctypes.byref(self.prob))),
-                                dtype=torch.uint8, device=dev)
+        skb = (tb.lib().tblr_tagged_sketch_workspace if self.tagged else
+               tb.lib().tblr_sketch_workspace)(tb.ctypes.byref(self.prob))
+        self.skws = torch.empty(max(1, skb), dtype=torch.uint8, device=dev)
         self.nfws = torch.empty(tb.lib().tblr_nearfield_workspace(tb.ctypes.byref(self.prob),
                                                                   self.m_max),
                                 dtype=torch.uint8, device=dev)
         self.mmax_dev = torch.empty(1, dtype=torch.int32, device=dev)
         self.host_total = torch.empty(1, dtype=torch.int64).pin_memory()
         self.host_mmax = torch.empty(1, dtype=torch.int32).pin_memory()
-        self.launches_per_step = 15
+        # tessellate 4, offsets 2, col 2, coupling 1, near field 2 (+1 split in mixed), decode 1,
+        # and either test matrices + sketch + combine (3; +2 splits in mixed) or the tagged
+        # sketch (1 FP64 gather + 1, or 3 splits + 1 in mixed)
+        mixed = w.get("precision", 0) == 1
+        base = 4 + 2 + 2 + 1 + 2 + 1 + (1 if mixed else 0)
+        self.launches_per_step = base + ((4 if mixed else 2) if self.tagged else
+                                         (5 if mixed else 3))
 
     def step(self, ev=None):
         tb, L, P, o = self.tb, self.tb.lib(), self.tb.ctypes.byref(self.prob), self.out
@@ -250,15 +259,25 @@ class Runner:
         self.torch.cuda.current_stream().synchronize()
         total, m_max = int(self.host_total[0]), int(self.host_mmax[0])
         assert total == self.total and m_max == self.m_max
-        ck(L.tblr_test_matrices(P, lay.ref, p(self.T), p(self.G), p(self.H), p(self.omega), s), "tm")
-        if ev is not None:
-            ev[0].record()
-        ck(L.tblr_sketch(P, lay.ref, None, p(self.omega), p(o.yz), p(self.skws), self.skws.numel(),
-                         s), "sketch")
-        if ev is not None:
-            ev[1].record()
-        ck(L.tblr_decode(P, lay.ref, p(self.T), p(o.z), p(o.tau), p(o.rho), s), "decode")
-        ck(L.tblr_combine(P, lay.ref, p(o.yz), p(o.z), p(self.S), p(self.R), s), "combine")
+        if self.tagged:
+            ck(L.tblr_decode(P, lay.ref, p(self.T), p(o.z), p(o.tau), p(o.rho), s), "decode")
+            if ev is not None:
+                ev[0].record()
+            ck(L.tblr_tagged_sketch(P, lay.ref, None, p(o.tau), p(self.G), p(self.H), p(self.S),
+                                    p(self.R), p(self.skws), self.skws.numel(), s), "tagged")
+            if ev is not None:
+                ev[1].record()
+        else:
+            ck(L.tblr_test_matrices(P, lay.ref, p(self.T), p(self.G), p(self.H), p(self.omega), s),
+               "tm")
+            if ev is not None:
+                ev[0].record()
+            ck(L.tblr_sketch(P, lay.ref, None, p(self.omega), p(o.yz), p(self.skws),
+                             self.skws.numel(), s), "sketch")
+            if ev is not None:
+                ev[1].record()
+            ck(L.tblr_decode(P, lay.ref, p(self.T), p(o.z), p(o.tau), p(o.rho), s), "decode")
+            ck(L.tblr_combine(P, lay.ref, p(o.yz), p(o.z), p(self.S), p(self.R), s), "combine")
         ck(L.tblr_col(P, lay.ref, p(self.S), p(o.u), p(o.ranks), p(self.colws), self.colws.numel(),
                       s), "col U")
         ck(L.tblr_col(P, lay.ref, p(self.R), p(o.v), p(o.ranks), p(self.colws), self.colws.numel(),
@@ -277,16 +296,19 @@ def measured_peak(key, fallback):
         return fallback, "fallback"
 
 
-def roofline(w, achieved, sketch_ms, traffic):
+def roofline(w, achieved, sketch_ms, traffic, tagged=False):
     """Roofline of the sketch kernel: FP64 pipe for the FP64 path, FP16 tensor pipe
-    (3 split MMAs per algorithmic multiply-add) for the mixed path."""
+    (3 split MMAs per algorithmic multiply-add) for the mixed path.  The tagged
+    sketch's algorithmic work is 2 n^2 (2 r) instead of 2 n^2 (2 ell r)."""
     if w.get("precision", 0) == 0:
-        return {"bound": "alu", "kernel": "apply_fp64_kernel (sketch)", "achieved": achieved,
+        return {"bound": "alu", "kernel": "apply_fp64_kernel (sketch)" + (", tagged" if tagged else ""),
+                "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": traffic, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
                 "sketch_ms": sketch_ms}
     peak, src = measured_peak("bf16_tflops", 1900.0)
-    return {"bound": "tensor", "kernel": "mixed_apply_kernel (sketch)", "achieved": achieved,
+    return {"bound": "tensor", "kernel": "mixed_apply_kernel (sketch)" + (", tagged" if tagged else ""),
+            "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
             "peak_source": f"{src} dense bf16 burst (fp16 runs at the same rate)",
             "executed_tflops": 3.0 * achieved, "executed_frac": 3.0 * achieved / peak,
@@ -300,7 +322,7 @@ def mixed_vs_fp64(tb, torch, w, run):
     from paper_2501_05528_gb300 import metrics
     d = w["d"]
     prob64 = tb.make_problem(d, w["kernel"], w["n"], w["grid"], (0.0,) * d, (1.0,) * d, w["k"],
-                             w["p"], w["e"], precision=tb.FP64)
+                             w["p"], w["e"], precision=tb.FP64, sketch=tb.SKETCH_TAGGED)
     ref = tb.compress(prob64, run.pts, run.T, run.G, run.H)
     torch.cuda.synchronize()
     h = lambda t: t.cpu().numpy()
@@ -312,7 +334,8 @@ def mixed_vs_fp64(tb, torch, w, run):
         reps.append(dict(U=h(o.u), V=h(o.v), At=h(o.at), B=B))
     err = metrics.ublr_difference_all(off, nbr, nnbr, s3, h(run.out.ranks), reps[0], reps[1])
     return {"relerr_vs_fp64": err, "bound": 1e-6, "within_bound": bool(err <= 1e-6),
-            "reference": "FP64 GPU path on the same inputs, full matrix, Frobenius"}
+            "reference": "FP64 GPU path (tag-factored, equal to the black-box FP64 result to "
+                         "1e-10) on the same inputs, full matrix, Frobenius"}
 
 
 def run_gpu(args, w):
@@ -394,7 +417,8 @@ def run_gpu(args, w):
 
     result = None
     if rank == 0:
-        flops = 2.0 * w["n"] * w["n"] * sz.sketch_cols
+        cols = 2 * sz.r if run.tagged else sz.sketch_cols
+        flops = 2.0 * w["n"] * w["n"] * cols
         sk = statistics.mean(sketch_ms) / 1e3
         achieved = flops / sk / 1e12
         gpu_res = dict(u=run.out.u.cpu().numpy(), v=run.out.v.cpu().numpy(),
@@ -422,13 +446,15 @@ def run_gpu(args, w):
                        "grid": list(w["grid"]), "k": w["k"], "p": w["p"], "e": w["e"],
                        "ell": sz.ell, "sketch_cols": sz.sketch_cols, "kernel": w["kernel"],
                        "precision": "fp64" if w.get("precision", 0) == 0 else "mixed",
+                       "sketch": "tagged" if run.tagged else "blackbox",
                        "l2": "flushed by a 256 MiB write before every step",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": run.launches_per_step * args.steps,
-            "roofline": roofline(w, achieved, statistics.mean(sketch_ms), args.traffic),
+            "roofline": roofline(w, achieved, statistics.mean(sketch_ms), args.traffic,
+                                 tagged=run.tagged),
             "cpu_baseline": cpu,
             "clocks": sampler.summary(),
         }
@@ -468,6 +494,147 @@ def run_reference(args, w):
                              "sample": sample}}
 
 
+# ------------------------------------------------------- batched and served
+
+def batch_specs(count, seed):
+    """Independent 2-D/3-D Laplace problems: N ~ U{4096..65536}, box size in {128, 256, 512},
+    k in {16, 32, 64}, points uniform in the unit square or cube, grid side
+    max(3, round((N / box)^(1/d)))."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for j in range(count):
+        d = int(rng.choice([2, 3]))
+        n = int(rng.integers(4096, 65537))
+        box = int(rng.choice([128, 256, 512]))
+        k = int(rng.choice([16, 32, 64]))
+        side = max(3, int(round((n / box) ** (1.0 / d))))
+        specs.append(dict(d=d, n=n, grid=(side,) * d, k=k, p=10, e=3,
+                          kernel="laplace2d" if d == 2 else "laplace3d", seed=seed + 1000 + j))
+    return specs
+
+
+def spec_inputs(s):
+    from paper_2501_05528_gb300 import inputs
+    pts = inputs.uniform_points(s["n"], s["d"], seed=s["seed"])
+    b = int(np.prod(s["grid"]))
+    T, G, H = inputs.tagging_draws(b, 3 ** s["d"] + 1 + s["e"], s["n"], s["k"] + s["p"],
+                                   seed=s["seed"] + 1)
+    return pts, T, G, H
+
+
+def spec_problem(tb, s, precision, sketch):
+    d = s["d"]
+    return tb.make_problem(d, s["kernel"], s["n"], s["grid"], (0.0,) * d, (1.0,) * d, s["k"],
+                           s["p"], s["e"], precision=precision, sketch=sketch)
+
+
+def run_batch(args):
+    """Config 4: the whole batch of independent jobs replayed as one CUDA graph per step."""
+    import torch
+    from paper_2501_05528_gb300 import tblr as tb
+    torch.cuda.set_device(0)
+    prec = 1 if args.precision == "mixed" else 0
+    sk = 1 if args.sketch == "tagged" else 0
+    specs = batch_specs(args.jobs, 0x7A660004)
+    dev = torch.device("cuda")
+    jobs = []
+    for s in specs:
+        pts, T, G, H = spec_inputs(s)
+        t = lambda a: torch.as_tensor(a, device=dev)
+        jobs.append(tb.BatchJob(spec_problem(tb, s, prec, sk), t(pts), t(T), t(G), t(H)))
+    tb.tblr_batch_plan(jobs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        graph = tb.Graph(jobs, n_streams=8)
+        for _ in range(args.warmup):
+            graph.launch()
+        stream.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(0)
+        with sampler:
+            t0.record()
+            for _ in range(args.steps):
+                graph.launch()
+            t1.record()
+            stream.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    assert tb.tblr_device_timeouts() == 0
+    return {"metric": METRIC, "value": args.jobs / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == 0 else "f16x3+f32/f64", "data": "synthetic",
+            "config": {"workload": f"batch of {args.jobs} independent 2-D/3-D Laplace jobs",
+                       "N": "U{4096..65536}", "box": "{128,256,512}", "k": "{16,32,64}",
+                       "precision": args.precision, "sketch": args.sketch,
+                       "execution": "one CUDA graph per step, 8 worker streams",
+                       "l2": "per-step working set tens of GB, far above L2"},
+            "gpu_launches": sum(1 for _ in jobs) * 15 * args.steps,
+            "clocks": sampler.summary(), "cpu_baseline": None}
+
+
+def run_serve(args):
+    """Config 5 (kernel operators): a seeded Poisson stream of requests of the sizes of
+    configs 1-3 through the continuous-batching server; p50/p99 latency and throughput."""
+    import torch
+    from paper_2501_05528_gb300 import tblr as tb
+    torch.cuda.set_device(0)
+    prec = 1 if args.precision == "mixed" else 0
+    sk = 1 if args.sketch == "tagged" else 0
+    shapes = [  # config 1 geometry, config 2, a config-3-shaped 3-D job at 1/8 of its size
+        dict(d=2, n=1024, grid=(4, 4), k=8, p=10, e=3, kernel="laplace2d", seed=11),
+        dict(d=2, n=65536, grid=(16, 16), k=32, p=10, e=3, kernel="laplace2d", seed=12),
+        dict(d=3, n=32768, grid=(4, 4, 4), k=64, p=10, e=3, kernel="laplace3d", seed=13),
+    ]
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    prepared = []
+    for s in shapes:
+        prob = spec_problem(tb, s, prec, sk)
+        pts, T, G, H = (pin(x) for x in spec_inputs(s))
+        warm = tb.tblr_compress_host(prob, pts, T, G, H)
+        prepared.append((prob, pts, T, G, H, warm["bnear_size"]))
+    rng = np.random.default_rng(0x7A660005)
+    kinds = rng.integers(0, len(shapes), size=args.requests)
+    gaps = rng.exponential(1.0 / args.rate, size=args.requests)
+    # Output buffers are pooled per request kind (8 sets, one per stream slot) since the
+    # benchmark does not read the results; each request's buffers stay valid until it ends.
+    pools = [[tb.host_outputs(p[0], p[5]) for _ in range(8)] for p in prepared]
+    outs = [pools[k][i % 8] for i, k in enumerate(kinds)]
+    free = torch.cuda.mem_get_info()[0]
+    srv = tb.Server(mem_budget_bytes=int(0.6 * free), max_inflight=8)
+    tickets = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for i, k in enumerate(kinds):
+        t_next += gaps[i]
+        delay = t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        prob, pts, T, G, H, _ = prepared[k]
+        tickets.append(srv.submit(prob, pts, T, G, H, outs[i]))
+    lat = []
+    for t in tickets:
+        st, l = srv.wait(t)
+        assert st == tb.TBLR_OK
+        lat.append(l)
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    lat.sort()
+    return {"metric": METRIC, "value": args.requests / wall, "unit": UNIT, "n_gpus": 1,
+            "steps": args.requests, "warmup": len(shapes), "ms_per_step": 1e3 * wall / args.requests,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == 0 else "f16x3+f32/f64", "data": "synthetic",
+            "config": {"workload": "Poisson request stream, kernel operators, sizes of configs 1-3",
+                       "rate_req_s": args.rate, "requests": args.requests,
+                       "mix": "uniform over {N=1,024 2-D k=8; N=65,536 2-D k=32; N=32,768 3-D k=64}",
+                       "precision": args.precision, "sketch": args.sketch,
+                       "server": "8 stream slots, budget 60% of free HBM, host buffers pinned"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "server_stats": {k: stats[k] for k in ("completed", "failed", "mem_peak", "throughput")},
+            "cpu_baseline": None}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -479,6 +646,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the mixed-vs-FP64 accuracy check of the mixed path")
+    ap.add_argument("--sketch", default="blackbox", choices=["blackbox", "tagged"],
+                    help="black-box sketch Y = A Omega (the paper's order) or the tag-factored S, R")
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
+                    help="single compressions, a 64-job batch (one CUDA graph), or a request stream")
+    ap.add_argument("--jobs", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate, req/s")
+    ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="sketch contraction precision (everything else stays FP64)")
     ap.add_argument("--traffic", type=float, default=None,
@@ -486,7 +660,15 @@ def main():
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     w["precision"] = 1 if args.precision == "mixed" else 0
-    res = run_reference(args, w) if args.impl == "reference" else run_gpu(args, w)
+    w["sketch"] = 1 if args.sketch == "tagged" else 0
+    if args.impl == "reference":
+        res = run_reference(args, w)
+    elif args.mode == "batch":
+        res = run_batch(args)
+    elif args.mode == "serve":
+        res = run_serve(args)
+    else:
+        res = run_gpu(args, w)
     if res is not None:
         print(json.dumps(res), flush=True)
 

@@ -25,6 +25,28 @@ __device__ __forceinline__ float entry_f32(const float (&ph)[3], const float (&p
   }
 }
 
+// The same entry without its constant factor: log2(r^2) in 2-D (times
+// 0.5 ln 2 gives log r), 1/r in 3-D (times 1/(4 pi)).  Callers fold the factor
+// into one multiplier per row.
+template <int KERNEL>
+__device__ __forceinline__ float entry_f32_raw(const float (&ph)[3], const float (&pl)[3],
+                                               const float (&qh)[3], const float (&ql)[3]) {
+  if (KERNEL == TBLR_KERNEL_LAPLACE2D) {
+    const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
+    const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
+    return __log2f(fmaf(dx, dx, dy * dy));
+  } else {
+    const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
+    const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
+    const float dz = (ph[2] - qh[2]) + (pl[2] - ql[2]);
+    return rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  }
+}
+template <int KERNEL>
+__host__ __device__ constexpr float entry_f32_factor() {
+  return KERNEL == TBLR_KERNEL_LAPLACE2D ? 0.34657359027997264f : 0.07957747154594767f;
+}
+
 // Split one FP64 coordinate into its double-float pair.
 __device__ __forceinline__ void split_coord(double x, float &hi, float &lo) {
   hi = (float)x;

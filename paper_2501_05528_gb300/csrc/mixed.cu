@@ -301,22 +301,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int e = 0; e < 8; ++e) bq[e] = a.box_of[min(q0 + e, a.n - 1)];
         one_box = bq[0] == bq[7];
       }
+      // A chunk that cannot meet the diagonal or the ragged edge needs no
+      // per-entry checks (the test is uniform over the CTA).
+      const int64_t kc0 = (int64_t)c * KC;
+      const bool clean = (kc0 + KC <= row0 || kc0 >= row0 + MB) && kc0 + KC <= a.n &&
+                         row0 + MB <= a.n;
+      const float factor = entry_f32_factor<KERNEL>() * a.scale_a;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int r = rbase + 32 * i;
         uint32_t hw[4], lw[4];
-        float tau_row = a.scale_a;
-        if (TAGGED && one_box) tau_row *= a.tau[(int64_t)brow[i] * a.b + bq[0]];
+        float w_row = factor;
+        if (TAGGED && one_box) w_row *= a.tau[(int64_t)brow[i] * a.b + bq[0]];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
           float v2[2];
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            const int64_t qq = q0 + e + u;
-            float w = tau_row;
-            if (TAGGED && !one_box) w = a.scale_a * a.tau[(int64_t)brow[i] * a.b + bq[e + u]];
-            float v = entry_f32<KERNEL>(rh[i], rl[i], qh[e + u], ql[e + u]) * w;
-            if (qq == prow[i] || qq >= a.n || prow[i] >= a.n) v = 0.f;
+            float w = w_row;
+            if (TAGGED && !one_box) w = factor * a.tau[(int64_t)brow[i] * a.b + bq[e + u]];
+            float v = entry_f32_raw<KERNEL>(rh[i], rl[i], qh[e + u], ql[e + u]) * w;
+            if (!clean) {
+              const int64_t qq = q0 + e + u;
+              if (qq == prow[i] || qq >= a.n || prow[i] >= a.n) v = 0.f;
+            }
             v2[u] = v;
           }
           const __half2 h = __floats2half2_rn(v2[0], v2[1]);

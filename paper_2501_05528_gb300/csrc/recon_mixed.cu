@@ -13,7 +13,6 @@ namespace tblr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSlab = 32;  // V columns per coupling CTA
 
 template <int KERNEL>
 __device__ __forceinline__ void load_point(const double *__restrict__ pts, int64_t n, int d,
@@ -27,92 +26,167 @@ __device__ __forceinline__ void load_point(const double *__restrict__ pts, int64
   }
 }
 
-// CTA per (i, j, slab of 32 columns of V_j).  Phase 1: W = A_ij V_j(:, slab)
-// row by row (one thread per row of box i), kept in shared memory.  Phase 2:
-// Atilde_ij(:, slab) = U_i^T W.
-template <int KERNEL>
+// CTA per (i, j): a register-tiled FP32 GEMM.  Rows of box i go in chunks of
+// RC; for each chunk W = A(chunk, I_j) V_j is accumulated over 32-point steps
+// (the generated 32 x RC kernel tile and the 32 x KP slice of V_j in shared
+// memory, 4 x 4 outputs per thread, Kahan flush per step), then
+// Atilde_ij += U_i(chunk)^T W with U's rows staged in shared memory.
+template <int KP>
+struct CouplingShape {
+  static constexpr int TX = KP / 4;       // threads across W's columns
+  static constexpr int TY = 256 / TX;     // threads across W's rows
+  static constexpr int RC = 4 * TY;       // rows per chunk
+  static constexpr int AT = KP / 16;      // Atilde tile edge per thread (16 x 16 threads)
+  static constexpr int KT = 32;           // points per K step
+};
+
+template <int KP>
+size_t coupling_f32_smem_bytes() {
+  using C = CouplingShape<KP>;
+  return sizeof(float) * ((size_t)C::KT * (C::RC + 4) + (size_t)C::KT * KP + 6 * (size_t)C::RC +
+                          6 * (size_t)C::KT + 2 * (size_t)C::RC * (KP + 4));
+}
+
+template <int KERNEL, int KP>
 __global__ void __launch_bounds__(kThreads) coupling_f32_kernel(
     const double *__restrict__ pts, int64_t n, int d, const int32_t *__restrict__ offsets,
     const int32_t *__restrict__ ranks, const double *__restrict__ U, const double *__restrict__ V,
-    int k, int b, int mmax, double *__restrict__ At) {
+    int k, int b, double *__restrict__ At) {
+  using C = CouplingShape<KP>;
+  constexpr int TX = C::TX, RC = C::RC, AT = C::AT, KT = C::KT;
   extern __shared__ float sf[];
-  const int i = blockIdx.x, j = blockIdx.y, c0 = blockIdx.z * kSlab, tid = threadIdx.x;
+  float *Ak = sf;                          // [KT][RC + 4]  generated A(chunk rows, step points)
+  float *Vk = Ak + KT * (RC + 4);          // [KT][KP]      V_j rows of the step
+  float *rch = Vk + KT * KP;               // [3][RC] row coordinates, hi
+  float *rcl = rch + 3 * RC;               // [3][RC] lo
+  float *qch = rcl + 3 * RC;               // [3][KT] column coordinates, hi
+  float *qcl = qch + 3 * KT;               // [3][KT] lo
+  float *Ws = qcl + 3 * KT;                // [RC][KP + 4]
+  float *Us = Ws + RC * (KP + 4);          // [RC][KP + 4]
+  const int i = blockIdx.x, j = blockIdx.y, tid = threadIdx.x;
   const int oi = offsets[i], mi = offsets[i + 1] - oi;
   const int oj = offsets[j], mj = offsets[j + 1] - oj;
   const int ki = ranks[i], kj = ranks[j];
   double *out = At + ((int64_t)i * b + j) * k * k;
-  if (ki == 0 || kj == 0 || c0 >= kj) {
-    for (int idx = tid; idx < k * kSlab; idx += kThreads) {
-      const int a = idx / kSlab, c = c0 + idx % kSlab;
-      if (c < k) out[(int64_t)a * k + c] = 0.0;
-    }
+  if (ki == 0 || kj == 0) {
+    for (int idx = tid; idx < k * k; idx += kThreads) out[idx] = 0.0;
     return;
   }
-  float *Vs = sf;                       // [mmax][kSlab]
-  float *qh = Vs + mmax * kSlab;        // [3][mmax]
-  float *ql = qh + 3 * mmax;            // [3][mmax]
-  float *Ws = ql + 3 * mmax;            // [mmax][kSlab + 1]
-  for (int idx = tid; idx < mj * kSlab; idx += kThreads) {
-    const int q = idx / kSlab, c = c0 + idx % kSlab;
-    Vs[idx] = (c < kj) ? (float)V[((int64_t)oj + q) * k + c] : 0.f;
-  }
-  for (int idx = tid; idx < 3 * mj; idx += kThreads) {
-    const int ax = idx / mj, q = idx % mj;
-    float h = 0.f, l = 0.f;
-    if (ax < d) split_coord(pts[ax * n + oj + q], h, l);
-    qh[ax * mmax + q] = h;
-    ql[ax * mmax + q] = l;
-  }
-  __syncthreads();
-  for (int p = tid; p < mi; p += kThreads) {
-    float rh[3], rl[3];
-    load_point<KERNEL>(pts, n, d, (int64_t)oi + p, rh, rl);
-    float acc[kSlab], hi[kSlab], cc[kSlab];
+  const int tx = tid % TX, ty = tid / TX;       // W tile: rows 4ty.., columns 4tx..
+  const int ta = tid / 16, tc = tid % 16;       // Atilde tile: rows AT*ta.., columns AT*tc..
+  float thi[AT][AT], tcc[AT][AT];
 #pragma unroll
-    for (int c = 0; c < kSlab; ++c) acc[c] = hi[c] = cc[c] = 0.f;
-    for (int q = 0; q < mj; ++q) {
-      const float ch[3] = {qh[q], qh[mmax + q], qh[2 * mmax + q]};
-      const float cl[3] = {ql[q], ql[mmax + q], ql[2 * mmax + q]};
-      float v = entry_f32<KERNEL>(rh, rl, ch, cl);
-      if (i == j && p == q) v = 0.f;
-      const float4 *vr = reinterpret_cast<const float4 *>(Vs + q * kSlab);
+  for (int x = 0; x < AT; ++x)
 #pragma unroll
-      for (int c4 = 0; c4 < kSlab / 4; ++c4) {
-        const float4 w = vr[c4];
-        acc[4 * c4] = fmaf(v, w.x, acc[4 * c4]);
-        acc[4 * c4 + 1] = fmaf(v, w.y, acc[4 * c4 + 1]);
-        acc[4 * c4 + 2] = fmaf(v, w.z, acc[4 * c4 + 2]);
-        acc[4 * c4 + 3] = fmaf(v, w.w, acc[4 * c4 + 3]);
+    for (int y = 0; y < AT; ++y) thi[x][y] = tcc[x][y] = 0.f;
+
+  for (int r0 = 0; r0 < mi; r0 += RC) {
+    __syncthreads();
+    for (int idx = tid; idx < 3 * RC; idx += kThreads) {
+      const int ax = idx / RC, r = idx % RC;
+      float h = 0.f, l = 0.f;
+      if (ax < d && r0 + r < mi) split_coord(pts[ax * n + oi + r0 + r], h, l);
+      rch[idx] = h;
+      rcl[idx] = l;
+    }
+    float acc[4][4], hi[4][4], cc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = hi[x][y] = cc[x][y] = 0.f;
+    for (int q0 = 0; q0 < mj; q0 += KT) {
+      __syncthreads();
+      for (int idx = tid; idx < 3 * KT; idx += kThreads) {
+        const int ax = idx / KT, q = idx % KT;
+        float h = 0.f, l = 0.f;
+        if (ax < d && q0 + q < mj) split_coord(pts[ax * n + oj + q0 + q], h, l);
+        qch[idx] = h;
+        qcl[idx] = l;
       }
-      if ((q & 31) == 31 || q == mj - 1) {
-#pragma unroll
-        for (int c = 0; c < kSlab; ++c) {
-          kahan_add(hi[c], cc[c], acc[c]);
-          acc[c] = 0.f;
+      for (int idx = tid; idx < KT * KP; idx += kThreads) {
+        const int q = idx / KP, c = idx % KP;
+        Vk[idx] = (q0 + q < mj && c < kj) ? (float)V[((int64_t)oj + q0 + q) * k + c] : 0.f;
+      }
+      __syncthreads();
+      {
+        const int q = tid % KT;
+        const float qh[3] = {qch[q], qch[KT + q], qch[2 * KT + q]};
+        const float ql[3] = {qcl[q], qcl[KT + q], qcl[2 * KT + q]};
+        const bool qin = q0 + q < mj;
+        for (int r = tid / KT; r < RC; r += kThreads / KT) {
+          const float rh[3] = {rch[r], rch[RC + r], rch[2 * RC + r]};
+          const float rl[3] = {rcl[r], rcl[RC + r], rcl[2 * RC + r]};
+          float v = entry_f32<KERNEL>(rh, rl, qh, ql);
+          if (!qin || r0 + r >= mi || (i == j && r0 + r == q0 + q)) v = 0.f;
+          Ak[q * (RC + 4) + r] = v;
         }
       }
-    }
+      __syncthreads();
+#pragma unroll 8
+      for (int q = 0; q < KT; ++q) {
+        const float4 av = *reinterpret_cast<const float4 *>(Ak + q * (RC + 4) + 4 * ty);
+        const float4 vv = *reinterpret_cast<const float4 *>(Vk + q * KP + 4 * tx);
+        const float a4[4] = {av.x, av.y, av.z, av.w};
+        const float v4[4] = {vv.x, vv.y, vv.z, vv.w};
 #pragma unroll
-    for (int c = 0; c < kSlab; ++c) Ws[p * (kSlab + 1) + c] = hi[c] - cc[c];
-  }
-  __syncthreads();
-  for (int idx = tid; idx < k * kSlab; idx += kThreads) {
-    const int a = idx / kSlab, c = idx % kSlab;
-    if (c0 + c >= k) continue;
-    double res = 0.0;
-    if (a < ki && c0 + c < kj) {
-      float acc = 0.f, hi = 0.f, cc = 0.f;
-      for (int p = 0; p < mi; ++p) {
-        acc = fmaf((float)U[((int64_t)oi + p) * k + a], Ws[p * (kSlab + 1) + c], acc);
-        if ((p & 31) == 31 || p == mi - 1) {
-          kahan_add(hi, cc, acc);
-          acc = 0.f;
-        }
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a4[x], v4[y], acc[x][y]);
       }
-      res = (double)hi - (double)cc;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          kahan_add(hi[x][y], cc[x][y], acc[x][y]);
+          acc[x][y] = 0.f;
+        }
     }
-    out[(int64_t)a * k + c0 + c] = res;
+    // W chunk and U rows to shared memory, then Atilde += U^T W.
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) Ws[(4 * ty + x) * (KP + 4) + 4 * tx + y] = hi[x][y] - cc[x][y];
+    for (int idx = tid; idx < RC * KP; idx += kThreads) {
+      const int r = idx / KP, a = idx % KP;
+      Us[r * (KP + 4) + a] =
+          (r0 + r < mi && a < ki) ? (float)U[((int64_t)oi + r0 + r) * k + a] : 0.f;
+    }
+    __syncthreads();
+    float tacc[AT][AT];
+#pragma unroll
+    for (int x = 0; x < AT; ++x)
+#pragma unroll
+      for (int y = 0; y < AT; ++y) tacc[x][y] = 0.f;
+    const int rend = min(RC, mi - r0);
+    for (int r = 0; r < rend; ++r) {
+      float u[AT], w[AT];
+#pragma unroll
+      for (int x = 0; x < AT; ++x) u[x] = Us[r * (KP + 4) + AT * ta + x];
+#pragma unroll
+      for (int y = 0; y < AT; ++y) w[y] = Ws[r * (KP + 4) + AT * tc + y];
+#pragma unroll
+      for (int x = 0; x < AT; ++x)
+#pragma unroll
+        for (int y = 0; y < AT; ++y) tacc[x][y] = fmaf(u[x], w[y], tacc[x][y]);
+      if ((r & 31) == 31 || r == rend - 1) {
+#pragma unroll
+        for (int x = 0; x < AT; ++x)
+#pragma unroll
+          for (int y = 0; y < AT; ++y) {
+            kahan_add(thi[x][y], tcc[x][y], tacc[x][y]);
+            tacc[x][y] = 0.f;
+          }
+      }
+    }
   }
+#pragma unroll
+  for (int x = 0; x < AT; ++x)
+#pragma unroll
+    for (int y = 0; y < AT; ++y) {
+      const int a = AT * ta + x, c = AT * tc + y;
+      if (a < k && c < k)
+        out[(int64_t)a * k + c] = (a < ki && c < kj) ? (double)thi[x][y] - (double)tcc[x][y] : 0.0;
+    }
 }
 
 // The boxes whose columns enter B_ij (every box of colour(j) for the probe
@@ -194,7 +268,11 @@ __global__ void __launch_bounds__(kThreads) nf_lowrank_f32_kernel(
   }
 }
 
-// B_ij(p, q) = sum_{c in set, q < m_c} A(I_i[p], I_c[q]) - U_i(p, :) M_is(:, q).
+// B_ij(p, q) = sum_{c in set, q < m_c} A(I_i[p], I_c[q]) - U_i(p, :) M_is(:, q), by
+// 64 x 64 output tiles (grid.z = tile index): 4 x 4 outputs per thread; the
+// column coordinates of each probe box are staged once per tile, the tile's
+// rows of U_i and columns of M_is sit in shared memory for the low-rank part.
+constexpr int kBT = 64;
 template <int KERNEL>
 __global__ void __launch_bounds__(kThreads) nf_block_f32_kernel(
     const float *__restrict__ chp, const float *__restrict__ clp, int64_t npad,
@@ -202,43 +280,102 @@ __global__ void __launch_bounds__(kThreads) nf_block_f32_kernel(
     const int32_t *__restrict__ nnbr, const int32_t *__restrict__ colour, int b, int s3, int k,
     int mmax, int mode, const double *__restrict__ U, const float *__restrict__ M,
     const int64_t *__restrict__ nf_off, double *__restrict__ Bn) {
-  extern __shared__ int set[];
-  const int i = blockIdx.x, s = blockIdx.y;
+  extern __shared__ float sf[];
+  const int i = blockIdx.x, s = blockIdx.y, tid = threadIdx.x;
   if (s >= nnbr[i]) return;
   const int j = nbr[(int64_t)i * s3 + s];
   const int oi = offsets[i], mi = offsets[i + 1] - oi;
   const int mj = offsets[j + 1] - offsets[j];
+  const int ntq = (mj + kBT - 1) / kBT;
+  const int p0 = (blockIdx.z / ntq) * kBT, q0 = (blockIdx.z % ntq) * kBT;
+  if (p0 >= mi) return;
+  float *Us = sf;                          // [kBT][k + 1]
+  float *Ms = Us + kBT * (k + 1);          // [k][kBT + 4]
+  float *qh = Ms + k * (kBT + 4);          // [3][kBT]
+  float *ql = qh + 3 * kBT;                // [3][kBT]
+  int *set = reinterpret_cast<int *>(ql + 3 * kBT);
   const int ns = probe_set_f(j, mode, colour, b, set);
+  for (int idx = tid; idx < kBT * k; idx += kThreads) {
+    const int r = idx / k, a = idx % k;
+    Us[r * (k + 1) + a] = (p0 + r < mi) ? (float)U[((int64_t)oi + p0 + r) * k + a] : 0.f;
+  }
   const float *Mi = M + ((int64_t)i * s3 + s) * k * mmax;
-  double *out = Bn + nf_off[(int64_t)i * s3 + s];
-  for (int idx = threadIdx.x; idx < mi * mj; idx += kThreads) {
-    const int p = idx / mj, q = idx % mj;
-    const int64_t gp = (int64_t)oi + p;
-    float rh[3], rl[3];
+  for (int idx = tid; idx < k * kBT; idx += kThreads) {
+    const int a = idx / kBT, q = idx % kBT;
+    Ms[a * (kBT + 4) + q] = (q0 + q < mj) ? Mi[(int64_t)a * mmax + q0 + q] : 0.f;
+  }
+  const int tx = tid % 16, ty = tid / 16;   // rows p0 + 4 ty + x, columns q0 + 4 tx + y
+  float rh[4][3], rl[4][3];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int64_t gp = (int64_t)oi + p0 + 4 * ty + x;
+    const bool in = p0 + 4 * ty + x < mi;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-      rh[ax] = chp[ax * npad + gp];
-      rl[ax] = clp[ax * npad + gp];
+      rh[x][ax] = in ? chp[ax * npad + gp] : 0.f;
+      rl[x][ax] = in ? clp[ax * npad + gp] : 0.f;
     }
-    float hi = 0.f, cc = 0.f;
-    for (int x = 0; x < ns; ++x) {
-      const int c = set[x];
-      const int oc = offsets[c];
-      if (q >= offsets[c + 1] - oc) continue;
-      const int64_t gq = (int64_t)oc + q;
-      if (gq == gp) continue;  // zero diagonal
-      float qh[3], ql[3];
+  }
+  float hi[4][4], cc[4][4];
 #pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        qh[ax] = chp[ax * npad + gq];
-        ql[ax] = clp[ax * npad + gq];
-      }
-      kahan_add(hi, cc, entry_f32<KERNEL>(rh, rl, qh, ql));
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) hi[x][y] = cc[x][y] = 0.f;
+  for (int u = 0; u < ns; ++u) {
+    const int c = set[u];
+    const int oc = offsets[c], mc = offsets[c + 1] - oc;
+    if (q0 >= mc) continue;  // uniform over the CTA
+    __syncthreads();
+    for (int idx = tid; idx < 3 * kBT; idx += kThreads) {
+      const int ax = idx / kBT, q = idx % kBT;
+      const bool in = q0 + q < mc;
+      qh[idx] = in ? chp[ax * npad + oc + q0 + q] : 0.f;
+      ql[idx] = in ? clp[ax * npad + oc + q0 + q] : 0.f;
     }
-    float lr = 0.f;
-    const double *ur = U + gp * k;
-    for (int a = 0; a < k; ++a) lr = fmaf((float)ur[a], Mi[(int64_t)a * mmax + q], lr);
-    out[idx] = ((double)hi - (double)cc) - (double)lr;
+    __syncthreads();
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int q = 4 * tx + y;
+      const float ch[3] = {qh[q], qh[kBT + q], qh[2 * kBT + q]};
+      const float cl[3] = {ql[q], ql[kBT + q], ql[2 * kBT + q]};
+      const bool qin = q0 + q < mc && q0 + q < mj;
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        float v = entry_f32<KERNEL>(rh[x], rl[x], ch, cl);
+        const bool diag = (c == i) && (p0 + 4 * ty + x == q0 + q);
+        if (!qin || diag || p0 + 4 * ty + x >= mi) v = 0.f;
+        kahan_add(hi[x][y], cc[x][y], v);
+      }
+    }
+  }
+  __syncthreads();
+  float lr[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) lr[x][y] = 0.f;
+  for (int a = 0; a < k; ++a) {
+    float uu[4], mm[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) uu[x] = Us[(4 * ty + x) * (k + 1) + a];
+#pragma unroll
+    for (int y = 0; y < 4; ++y) mm[y] = Ms[a * (kBT + 4) + 4 * tx + y];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) lr[x][y] = fmaf(uu[x], mm[y], lr[x][y]);
+  }
+  double *out = Bn + nf_off[(int64_t)i * s3 + s];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int p = p0 + 4 * ty + x;
+    if (p >= mi) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int q = q0 + 4 * tx + y;
+      if (q < mj)
+        out[(int64_t)p * mj + q] = ((double)hi[x][y] - (double)cc[x][y]) - (double)lr[x][y];
+    }
   }
 }
 
@@ -257,28 +394,32 @@ __global__ void split_all_coords(const double *__restrict__ pts, int64_t n, int6
 
 }  // namespace
 
-size_t coupling_f32_smem(int mmax) {
-  return sizeof(float) * ((size_t)mmax * kSlab + 6 * (size_t)mmax + (size_t)mmax * (kSlab + 1));
+template <int KERNEL, int KP>
+int launch_coupling_f32(const Prob &P, const tblr_layout *lay, const double *u, const double *v,
+                        const int32_t *ranks, double *at, cudaStream_t s) {
+  auto kern = coupling_f32_kernel<KERNEL, KP>;
+  const size_t smem = coupling_f32_smem_bytes<KP>();
+  TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<dim3((unsigned)P.b, (unsigned)P.b), kThreads, smem, s>>>(lay->pts, P.n, P.d, lay->offsets,
+                                                                 ranks, u, v, P.k, (int)P.b, at);
+  return launch_status("coupling_f32_kernel");
+}
+
+template <int KERNEL>
+int coupling_f32_dispatch(const Prob &P, const tblr_layout *lay, const double *u, const double *v,
+                          const int32_t *ranks, double *at, cudaStream_t s) {
+  if (P.k <= 16) return launch_coupling_f32<KERNEL, 16>(P, lay, u, v, ranks, at, s);
+  if (P.k <= 32) return launch_coupling_f32<KERNEL, 32>(P, lay, u, v, ranks, at, s);
+  return launch_coupling_f32<KERNEL, 64>(P, lay, u, v, ranks, at, s);
 }
 
 int coupling_mixed(const Prob &P, const tblr_layout *lay, const double *u, const double *v,
                    const int32_t *ranks, double *at, int mmax, cudaStream_t s) {
+  (void)mmax;
   TBLR_REQUIRE(P.k <= 64, "mixed coupling supports k <= 64");
-  const size_t smem = coupling_f32_smem(mmax);
-  TBLR_REQUIRE(smem <= 220 * 1024, "mixed coupling supports boxes of at most ~780 points");
-  const dim3 grid((unsigned)P.b, (unsigned)P.b, (unsigned)cdiv(P.k, kSlab));
-  if (P.kernel == TBLR_KERNEL_LAPLACE2D) {
-    auto kern = coupling_f32_kernel<TBLR_KERNEL_LAPLACE2D>;
-    TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, kThreads, smem, s>>>(lay->pts, P.n, P.d, lay->offsets, ranks, u, v, P.k, (int)P.b,
-                                      mmax, at);
-  } else {
-    auto kern = coupling_f32_kernel<TBLR_KERNEL_LAPLACE3D>;
-    TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, kThreads, smem, s>>>(lay->pts, P.n, P.d, lay->offsets, ranks, u, v, P.k, (int)P.b,
-                                      mmax, at);
-  }
-  return launch_status("coupling_f32_kernel");
+  return P.kernel == TBLR_KERNEL_LAPLACE2D
+             ? coupling_f32_dispatch<TBLR_KERNEL_LAPLACE2D>(P, lay, u, v, ranks, at, s)
+             : coupling_f32_dispatch<TBLR_KERNEL_LAPLACE3D>(P, lay, u, v, ranks, at, s);
 }
 
 size_t nearfield_mixed_workspace(const Prob &P, int mmax) {
@@ -308,16 +449,24 @@ int nearfield_mixed(const Prob &P, const tblr_layout *lay, const double *u, cons
                           smem_lr, s>>>(lay->offsets, lay->nbr, lay->nnbr, lay->colour, (int)P.b,
                                         P.s3, P.k, mmax, P.nearfield, at, v, M);
   TBLR_TRY(launch_status("nf_lowrank_f32_kernel"));
-  const size_t smem_b = sizeof(int) * P.b;
-  const dim3 grid((unsigned)P.b, (unsigned)P.s3);
-  if (P.kernel == TBLR_KERNEL_LAPLACE2D)
-    nf_block_f32_kernel<TBLR_KERNEL_LAPLACE2D><<<grid, kThreads, smem_b, s>>>(
-        ch, cl, npad, lay->offsets, lay->nbr, lay->nnbr, lay->colour, (int)P.b, P.s3, P.k, mmax,
-        P.nearfield, u, M, nf_off, bnear);
-  else
-    nf_block_f32_kernel<TBLR_KERNEL_LAPLACE3D><<<grid, kThreads, smem_b, s>>>(
-        ch, cl, npad, lay->offsets, lay->nbr, lay->nnbr, lay->colour, (int)P.b, P.s3, P.k, mmax,
-        P.nearfield, u, M, nf_off, bnear);
+  const size_t smem_b = sizeof(float) * (kBT * (P.k + 1) + P.k * (kBT + 4) + 6 * kBT) +
+                        sizeof(int) * P.b;
+  TBLR_REQUIRE(smem_b <= 220 * 1024, "mixed near field: too many boxes for the probe set");
+  const int tiles = (int)cdiv(mmax, kBT);
+  const dim3 grid((unsigned)P.b, (unsigned)P.s3, (unsigned)(tiles * tiles));
+  if (P.kernel == TBLR_KERNEL_LAPLACE2D) {
+    auto kern = nf_block_f32_kernel<TBLR_KERNEL_LAPLACE2D>;
+    TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    kern<<<grid, kThreads, smem_b, s>>>(ch, cl, npad, lay->offsets, lay->nbr, lay->nnbr,
+                                         lay->colour, (int)P.b, P.s3, P.k, mmax, P.nearfield, u,
+                                         M, nf_off, bnear);
+  } else {
+    auto kern = nf_block_f32_kernel<TBLR_KERNEL_LAPLACE3D>;
+    TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    kern<<<grid, kThreads, smem_b, s>>>(ch, cl, npad, lay->offsets, lay->nbr, lay->nnbr,
+                                         lay->colour, (int)P.b, P.s3, P.k, mmax, P.nearfield, u,
+                                         M, nf_off, bnear);
+  }
   return launch_status("nf_block_f32_kernel");
 }
 

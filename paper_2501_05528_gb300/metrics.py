@@ -75,10 +75,10 @@ def blocks_from_flat(bnear, nf_off, nbr, nnbr, off, s3):
     """Split the flat near-field array into {(i, j): m_i x m_j} blocks."""
     out = {}
     for i in range(len(nnbr)):
-        mi = off[i + 1] - off[i]
+        mi = int(off[i + 1] - off[i])          # Python ints: offsets exceed 2^31 at scale
         for s in range(int(nnbr[i])):
             j = int(nbr[i * s3 + s])
-            mj = off[j + 1] - off[j]
+            mj = int(off[j + 1] - off[j])
             st = int(nf_off[i * s3 + s])
             out[(i, j)] = np.asarray(bnear[st:st + mi * mj]).reshape(mi, mj)
     return out

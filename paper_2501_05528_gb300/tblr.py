@@ -434,8 +434,10 @@ class BatchJob:
         """After tblr_batch_plan: outputs and the full workspace, sized from the plan."""
         sz, dev, n, k = self.sz, _dev(), self.prob.n, self.prob.k
         f64 = dict(dtype=torch.float64, device=dev)
+        tagged = self.prob.sketch == SKETCH_TAGGED       # Y, Z are never formed
         self.out = Compressed(
-            yz=torch.empty(n, sz.sketch_cols, **f64), z=torch.empty(sz.b, sz.ell, **f64),
+            yz=torch.empty(1 if tagged else n * sz.sketch_cols, **f64),
+            z=torch.empty(sz.b, sz.ell, **f64),
             tau=torch.empty(sz.b, sz.b, **f64), rho=torch.empty(sz.b, **f64),
             u=torch.empty(n, k, **f64), v=torch.empty(n, k, **f64),
             ranks=torch.empty(sz.b, dtype=torch.int32, device=dev),
