@@ -42,6 +42,11 @@ __device__ __forceinline__ float entry_f32_raw(const float (&ph)[3], const float
     return rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
   }
 }
+// The raw entry from the squared distance r2 (FP32).
+template <int KERNEL>
+__device__ __forceinline__ float entry_f32_of_r2(float r2) {
+  return KERNEL == TBLR_KERNEL_LAPLACE2D ? __log2f(r2) : rsqrtf(r2);
+}
 template <int KERNEL>
 __host__ __device__ constexpr float entry_f32_factor() {
   return KERNEL == TBLR_KERNEL_LAPLACE2D ? 0.34657359027997264f : 0.07957747154594767f;

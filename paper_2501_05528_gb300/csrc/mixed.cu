@@ -1,23 +1,34 @@
 // Mixed-precision black-box apply Y = A X on tcgen05 tensor cores (sm_103a).
 //
-// Split precision: X = Xh + Xl and A = Ah + Al with FP16 parts (11-bit
-// significands each), and A X ~ Ah Xh + Ah Xl + Al Xh, three FP16 MMAs with
-// FP32 accumulation (the dropped Al Xl term is ~2^-22 relative).  Tensor-core
-// FP32 accumulation is flushed every `flush` K chunks (64 points each) into a
-// Kahan-compensated FP32 sum kept in TMEM, so the long K = n reduction keeps
+// Split precision: every operand value v is carried as three BF16 parts,
+// v = h + m + l with |v - h - m - l| <= 2^-24 |v| (each part rounds the
+// remainder of the previous one to 8 significant bits; BF16 keeps the FP32
+// exponent range, so no scaling is needed and nothing underflows or
+// overflows).  A X is then the sum of six BF16 products with FP32
+// accumulation:
+//   l*h + m*m + h*l   (~2^-16 relative)   issued first,
+//   m*h + h*m         (~2^-8)             next,
+//   h*h                                   last,
+// dropping m*l, l*m and l*l (<= 2^-24).  Issuing the small terms first keeps
+// the roundings of the tensor-core adder (which truncates) on small partial
+// sums: only the four h*h steps of a K chunk round at the size of the chunk's
+// sum.  The FP32 accumulator is flushed every `flush` K chunks (64 points) into
+// a Kahan-compensated FP32 sum kept in TMEM, so the long K = n reduction keeps
 // ~2^-40 accumulation error; the result is written in FP64.
 //
-// One CTA computes a 128-row x 128-column tile of Y over all n points:
-//   warp 0      TMA producer: FP16 hi/lo tiles of X (128 columns x 64 points)
+// One CTA computes a 128-row x NBT-column tile of Y over all n points:
+//   warp 0      TMA producer: BF16 h/m/l tiles of X (NBT columns x 64 points)
 //   warp 1      TMEM allocator and single-thread MMA issuer
 //   warps 2-5   epilogue: drain the FP32 accumulator into the Kahan sums
 //   warps 6-13  generators: evaluate the 128 x 64 kernel tile A(rows, chunk)
-//               from double-float coordinates, split it into FP16 hi/lo and
+//               from double-float coordinates, split it into BF16 h/m/l and
 //               write it in the 128-byte-swizzled K-major operand layout
-// Stages of shared memory (3 x 64 KiB) and two TMEM accumulators let the
-// generators, the TMA, the tensor core and the epilogue overlap.  Every
-// mbarrier wait is bounded by a clock budget; a timeout is counted in a device
-// counter (read by tblr_device_timeouts) and the CTA drains and exits.
+// Two or three stages of shared memory and (for NBT <= 128) two TMEM
+// accumulators let the generators, the TMA, the tensor core and the epilogue
+// overlap; NBT = 160 (up to 160 sketch columns in one tile, so each kernel
+// tile is generated once) has one accumulator.  Every mbarrier wait is bounded
+// by a clock budget; a timeout is counted in a device counter (read by
+// tblr_device_timeouts) and the CTA drains and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <stdlib.h>
@@ -35,24 +46,62 @@ static __device__ unsigned int g_mixed_timeouts;
 namespace {
 
 constexpr int MB = 128;   // tile rows
-constexpr int NB = 128;   // tile columns
-constexpr int KC = 64;    // points per K chunk
-constexpr int STAGES = 3;
+constexpr int KC = 64;    // points per K chunk (one 128-byte BF16 row)
+constexpr int kMaxNB = 160;
+constexpr int kParts = 3;  // BF16 parts per operand value
 constexpr int kGenWarps = 8;
 constexpr int kEpiWarps = 4;
-constexpr int kThreads = 32 * (2 + kEpiWarps + kGenWarps);
+constexpr int kStageWarp = 2 + kEpiWarps + kGenWarps;  // stages point data
+constexpr int kThreads = 32 * (kStageWarp + 1);
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitBudget = 1000000000LL;  // clock cycles (~0.5 s) per wait
-constexpr int kTileBytes = MB * 128;             // one FP16 plane of a tile
+constexpr int kTileBytes = MB * 128;             // one BF16 part of an A tile
+constexpr int kSmemLimit = 232448;               // 227 KiB of opt-in shared memory per CTA
+constexpr int kCS = 3;      // slots of staged point data (the producer runs kCS - 1 chunks ahead)
+constexpr int kMaxRB = 4;   // row boxes per CTA with staged tag weights (else gathered)
+constexpr int kCoordBytes = kCS * (KC / 2 * 12 * 4 + kMaxRB * KC * 4 + KC * 4);
+
+// Shared-memory stages and TMEM accumulators for an NBT-column tile.  The
+// tile's columns are accumulated in H units of UC = NBT / H columns; units
+// (chunk group g, part h) take turns in two TMEM slots, so the tensor core
+// fills one slot while the epilogue drains the other.  NBT <= 128: one unit
+// per tile (a double-buffered accumulator); NBT = 160: two units of 80.
+template <int NBT>
+struct Cfg {
+  static constexpr int kStageBytes = kParts * (kTileBytes + NBT * 128);
+  static constexpr int STAGES = (kSmemLimit - 2048 - kCoordBytes) / kStageBytes >= 3 ? 3 : 2;
+  static constexpr int H = 4 * NBT <= (int)kTmemCols ? 1 : 2;
+  static constexpr int UC = NBT / H;
+  static_assert(NBT % 32 == 0 && NBT <= kMaxNB, "tile width");
+  static_assert(UC % 16 == 0 && (UC * 128) % 1024 == 0, "unit width");
+  static_assert(STAGES * kStageBytes + kCoordBytes + 2048 <= kSmemLimit, "shared memory");
+  static_assert(2 * UC + 2 * NBT <= (int)kTmemCols, "tensor memory");
+};
 
 template <int NBT>
 struct __align__(1024) Smem {
-  uint8_t a[STAGES][2][kTileBytes];  // A hi, A lo: 128 rows x 128 bytes
-  uint8_t x[STAGES][2][NBT * 128];   // X hi, X lo: NBT rows x 128 bytes
+  static constexpr int STAGES = Cfg<NBT>::STAGES;
+  uint8_t a[STAGES][kParts][kTileBytes];  // A h, m, l: 128 rows x 128 bytes
+  uint8_t x[STAGES][kParts][NBT * 128];   // X h, m, l: NBT rows x 128 bytes
+  // Point data of a chunk, staged by the producer warp.  Point pair
+  // P = 4 j + pr (points 2P, 2P + 1) sits at [pr][j], so the 8 pairs a warp
+  // reads at once are 8 consecutive 16-byte (or 8-byte) words: no bank
+  // conflicts.  qc: negated coordinates as three float4 fields
+  // {xh, yh}, {zh, xl}, {yl, zl} (each a pair of the two points); wt: the
+  // kernel factor times the tag weight per row box and pair; bq: the column
+  // box of each point.
+  float4 qc[kCS][3][4][8];
+  float2 wt[kCS][kMaxRB][4][8];
+  int bq[kCS][KC];
+  uint64_t cfull[kCS], cfree[kCS];
   uint64_t full_a[STAGES], full_b[STAGES], empty[STAGES];
   uint64_t dfull[2], dempty[2], done;
   uint32_t tmem_base;
   volatile int abort;
+};
+
+struct Maps {
+  CUtensorMap part[kParts];  // X h, m, l planes
 };
 
 struct MixedArgs {
@@ -68,8 +117,6 @@ struct MixedArgs {
   const float *tau;
   const int32_t *box_of;
   int b;
-  float scale_a;
-  double unscale;
   volatile int *status;  // set to 1 by any timed-out wait of this launch
 };
 
@@ -93,12 +140,43 @@ __device__ __forceinline__ bool wait_or_abort(SM &S, volatile int *status, uint6
   }
 }
 
+// Warp-uniform bounded wait: lane 0 polls, every lane gets its verdict (so a
+// warp never splits on a timeout), and the warp barrier orders the lanes'
+// later accesses after the observed phase.
+template <class SM>
+__device__ __forceinline__ bool warp_wait(SM &S, volatile int *status, uint64_t *bar,
+                                          uint32_t parity) {
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) ok = wait_or_abort(S, status, bar, parity);
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok;
+}
+template <class SM>
+__device__ __forceinline__ bool warp_aborted(SM &S) {
+  return __shfl_sync(0xffffffffu, S.abort, 0) != 0;
+}
+
+// Three-way BF16 split of two FP32 values, packed as K-adjacent pairs.  The
+// remainders v - h and (v - h) - m are exact in FP32.
+__device__ __forceinline__ void split3(float v0, float v1, uint32_t &h, uint32_t &m, uint32_t &l) {
+  const __nv_bfloat162 bh = __floats2bfloat162_rn(v0, v1);
+  const float2 fh = __bfloat1622float2(bh);
+  const float r0 = v0 - fh.x, r1 = v1 - fh.y;
+  const __nv_bfloat162 bm = __floats2bfloat162_rn(r0, r1);
+  const float2 fm = __bfloat1622float2(bm);
+  const __nv_bfloat162 bl = __floats2bfloat162_rn(r0 - fm.x, r1 - fm.y);
+  h = *reinterpret_cast<const uint32_t *>(&bh);
+  m = *reinterpret_cast<const uint32_t *>(&bm);
+  l = *reinterpret_cast<const uint32_t *>(&bl);
+}
+
 template <int KERNEL, int NBT, bool TAGGED>
 __global__ void __launch_bounds__(kThreads, 1)
-    mixed_apply_kernel(const __grid_constant__ CUtensorMap map_hi,
-                       const __grid_constant__ CUtensorMap map_lo, MixedArgs a) {
+    mixed_apply_kernel(const __grid_constant__ Maps maps, MixedArgs a) {
   extern __shared__ uint8_t smem_raw[];
   using SM = Smem<NBT>;
+  constexpr int STAGES = Cfg<NBT>::STAGES, H = Cfg<NBT>::H, UC = Cfg<NBT>::UC;
   SM &S = *reinterpret_cast<SM *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                   ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -123,15 +201,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&S.dfull[d], 1);
       tc::mbar_init(&S.dempty[d], kEpiWarps);
     }
+    for (int t = 0; t < kCS; ++t) {
+      tc::mbar_init(&S.cfull[t], 1);
+      tc::mbar_init(&S.cfree[t], kGenWarps);
+    }
     tc::mbar_init(&S.done, 1);
     tc::fence_mbar_init();
-    tc::tma_prefetch(&map_hi);
-    tc::tma_prefetch(&map_lo);
+    for (int t = 0; t < kParts; ++t) tc::tma_prefetch(&maps.part[t]);
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = S.tmem_base;
+  // Boxes of this tile's rows (rows are box-major, so they form a range).
+  const int n32 = (int)a.n;
+  const int rb0 = TAGGED ? a.box_of[(int)row0] : 0;
+  const int nrb = TAGGED ? a.box_of[min((int)row0 + MB, n32) - 1] - rb0 + 1 : 1;
+  const bool staged_w = nrb <= kMaxRB;
+  const float factor = entry_f32_factor<KERNEL>();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -141,9 +228,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = c % STAGES;
         const uint32_t ph = (c / STAGES) & 1;
         if (c >= STAGES && !wait_or_abort(S, a.status, &S.empty[s], ph ^ 1)) break;
-        tc::mbar_arrive_expect_tx(&S.full_b[s], 2 * NBT * 128);
-        tc::tma_load_2d(S.x[s][0], &map_hi, &S.full_b[s], c * KC, col0);
-        tc::tma_load_2d(S.x[s][1], &map_lo, &S.full_b[s], c * KC, col0);
+        tc::mbar_arrive_expect_tx(&S.full_b[s], kParts * NBT * 128);
+#pragma unroll
+        for (int t = 0; t < kParts; ++t)
+          tc::tma_load_2d(S.x[s][t], &maps.part[t], &S.full_b[s], c * KC, col0);
         issued = c + 1;
       }
       // Copies still in flight must land before the CTA exits.
@@ -157,31 +245,52 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_f16_f32(MB, NBT);
-      for (int c = 0; c < nk && !S.abort; ++c) {
+      const uint32_t idesc = tc::idesc_bf16_f32(MB, UC);
+      bool ok = true;
+      for (int c = 0; c < nk && ok && !S.abort; ++c) {
         const int s = c % STAGES;
         const uint32_t ph = (c / STAGES) & 1;
-        const int g = c / flush, d = g & 1;
+        const int g = c / flush;
         const bool first = (c % flush) == 0;
         const bool last = (c % flush) == flush - 1 || c == nk - 1;
-        if (first && g >= 2 && !wait_or_abort(S, a.status, &S.dempty[d], ((g >> 1) - 1) & 1)) break;
         if (!wait_or_abort(S, a.status, &S.full_a[s], ph)) break;
         if (!wait_or_abort(S, a.status, &S.full_b[s], ph)) break;
         tc::tc_fence_after();
-        const uint32_t ah = tc::smem_u32(S.a[s][0]), al = tc::smem_u32(S.a[s][1]);
-        const uint32_t bh = tc::smem_u32(S.x[s][0]), bl = tc::smem_u32(S.x[s][1]);
-        const uint32_t dt = tmem + d * NBT;
+        // Operand descriptors of the stage's parts; a K step of 16 BF16 (32
+        // bytes) or a unit's row offset only moves the start-address field.
+        uint64_t ad[kParts], bd[kParts];
 #pragma unroll
-        for (int kk = 0; kk < KC / 16; ++kk) {
-          const uint32_t off = kk * 32;  // 16 FP16 along K inside the 128-byte row
-          const uint64_t dah = tc::sw128_desc(ah + off), dal = tc::sw128_desc(al + off);
-          const uint64_t dbh = tc::sw128_desc(bh + off), dbl = tc::sw128_desc(bl + off);
-          tc::mma_f16(dt, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
-          tc::mma_f16(dt, dah, dbl, idesc, 1u);
-          tc::mma_f16(dt, dal, dbh, idesc, 1u);
+        for (int t = 0; t < kParts; ++t) {
+          ad[t] = tc::sw128_desc(tc::smem_u32(S.a[s][t]));
+          bd[t] = tc::sw128_desc(tc::smem_u32(S.x[s][t]));
         }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          const int u = g * H + h, slot = u & 1, use = u >> 1;
+          // The slot is free once the epilogue drained its previous unit.
+          if (first && use >= 1 && !wait_or_abort(S, a.status, &S.dempty[slot], (use - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          if (first && use >= 1) tc::tc_fence_after();
+          const uint32_t dt = tmem + slot * UC;
+          const uint64_t boff = (uint64_t)(h * UC * 128) >> 4;
+          uint32_t acc = first ? 0u : 1u;
+          // (A part, X part) products, smallest first.
+          constexpr int kOrder[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
+#pragma unroll
+          for (int o = 0; o < 6; ++o) {
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk) {
+              tc::mma_f16(dt, ad[kOrder[o][0]] + 2 * kk, bd[kOrder[o][1]] + boff + 2 * kk, idesc,
+                          acc);
+              acc = 1u;
+            }
+          }
+          if (last) tc::mma_commit(&S.dfull[slot]);
+        }
+        if (!ok) break;
         tc::mma_commit(&S.empty[s]);
-        if (last) tc::mma_commit(&S.dfull[d]);
       }
       // Every MMA issued so far has finished once `done` completes.
       tc::mma_commit(&S.done);
@@ -194,56 +303,56 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
-    const uint32_t hi_t = tmem + 2 * NBT + lanes, cc_t = tmem + 3 * NBT + lanes;
-    float hv[32], cv[32], dv[32];
+    const uint32_t hi_t = tmem + 2 * UC + lanes, cc_t = hi_t + NBT;
+    float hv[16], cv[16], dv[16];
 #pragma unroll
-    for (int t = 0; t < 32; ++t) hv[t] = 0.f;
+    for (int t = 0; t < 16; ++t) hv[t] = 0.f;
 #pragma unroll
-    for (int cg = 0; cg < NBT / 32; ++cg) {
-      tc::tmem_st32(hi_t + cg * 32, hv);
-      tc::tmem_st32(cc_t + cg * 32, hv);
+    for (int cg = 0; cg < NBT / 16; ++cg) {
+      tc::tmem_st16(hi_t + cg * 16, hv);
+      tc::tmem_st16(cc_t + cg * 16, hv);
     }
     tc::tmem_wait_st();
-    bool ok = !S.abort;
+    bool ok = !warp_aborted(S);
     for (int g = 0; g < ngroups && ok; ++g) {
-      const int d = g & 1;
-      if (!wait_or_abort(S, a.status, &S.dfull[d], (g >> 1) & 1)) {
-        ok = false;
-        break;
-      }
-      tc::tc_fence_after();
-      const uint32_t d_t = tmem + d * NBT + lanes;
-#pragma unroll 1
-      for (int cg = 0; cg < NBT / 32; ++cg) {
-        tc::tmem_ld32(d_t + cg * 32, dv);
-        tc::tmem_ld32(hi_t + cg * 32, hv);
-        tc::tmem_ld32(cc_t + cg * 32, cv);
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {  // Kahan: hi + (d - c), c keeps the lost low part
-          const float yv = dv[t] - cv[t];
-          const float tt = hv[t] + yv;
-          cv[t] = (tt - hv[t]) - yv;
-          hv[t] = tt;
+      for (int h = 0; h < H; ++h) {
+        const int u = g * H + h, slot = u & 1;
+        if (!warp_wait(S, a.status, &S.dfull[slot], (u >> 1) & 1)) {
+          ok = false;
+          break;
         }
-        tc::tmem_st32(hi_t + cg * 32, hv);
-        tc::tmem_st32(cc_t + cg * 32, cv);
+        tc::tc_fence_after();
+        const uint32_t d_t = tmem + slot * UC + lanes;
+#pragma unroll 1
+        for (int cg = 0; cg < UC / 16; ++cg) {
+          const uint32_t col = h * UC + cg * 16;
+          tc::tmem_ld16x3(d_t + cg * 16, hi_t + col, cc_t + col, dv, hv, cv);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {  // Kahan: hi + (d - c), c keeps the lost low part
+            const float yv = dv[t] - cv[t];
+            const float tt = hv[t] + yv;
+            cv[t] = (tt - hv[t]) - yv;
+            hv[t] = tt;
+          }
+          tc::tmem_st16(hi_t + col, hv);
+          tc::tmem_st16(cc_t + col, cv);
+        }
+        tc::tmem_wait_st();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&S.dempty[slot]);
       }
-      tc::tmem_wait_st();
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&S.dempty[d]);
     }
     if (ok) {
       const int64_t p = row0 + 32 * q + lane;
 #pragma unroll 1
-      for (int cg = 0; cg < NBT / 32; ++cg) {
-        tc::tmem_ld32(hi_t + cg * 32, hv);
-        tc::tmem_ld32(cc_t + cg * 32, cv);
+      for (int cg = 0; cg < NBT / 16; ++cg) {
+        tc::tmem_ld16x2(hi_t + cg * 16, cc_t + cg * 16, hv, cv);
         if (p < a.n) {
 #pragma unroll
-          for (int t = 0; t < 32; ++t) {
-            const int64_t c = (int64_t)col0 + cg * 32 + t;
-            const double val = ((double)hv[t] - (double)cv[t]) * a.unscale;
+          for (int t = 0; t < 16; ++t) {
+            const int64_t c = (int64_t)col0 + cg * 16 + t;
+            const double val = (double)hv[t] - (double)cv[t];
             if (c < a.split)
               a.y[p * a.ldy + c] = val;
             else if (c < a.ncols)
@@ -252,94 +361,125 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else {
+  } else if (warp < kStageWarp) {
     // ---------------------------------------------------------- generators
+    // Thread (j, rbase): rows rbase + 32 i (i < 4) x points 8 j .. 8 j + 7 of
+    // each chunk, two points at a time in packed FP32x2 arithmetic.
     const int gt = tid - 32 * (2 + kEpiWarps);  // 0 .. 255
     const int j = gt & 7;                        // 16-byte chunk (8 points) within the 64
-    const int rbase = gt >> 3;                   // rows rbase + 32 i, i = 0..3
-    float rh[4][3], rl[4][3];
-    int64_t prow[4];
-    int brow[4];
+    const int rbase = gt >> 3;
+    const int prow0 = (int)row0 + rbase;         // n < 2^30 is checked on the host
+    float2 rx[4][3], lx[4][3];                   // row coordinates, hi and lo, as (v, v) pairs
+    int rbi[4], brow[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      prow[i] = row0 + rbase + 32 * i;
-      brow[i] = (TAGGED && prow[i] < a.n) ? a.box_of[prow[i]] : 0;
+      const int p = prow0 + 32 * i;
+      const int bx = (TAGGED && p < n32) ? a.box_of[p] : rb0;
+      rbi[i] = bx - rb0;
+      brow[i] = bx * a.b;
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
-        const bool in = ax < a.d && prow[i] < a.n;
-        rh[i][ax] = in ? a.ch[ax * a.npad + prow[i]] : 0.f;
-        rl[i][ax] = in ? a.cl[ax * a.npad + prow[i]] : 0.f;
+        const bool in = ax < a.d && p < n32;
+        const float h = in ? a.ch[ax * a.npad + p] : 0.f;
+        const float l = in ? a.cl[ax * a.npad + p] : 0.f;
+        rx[i][ax] = make_float2(h, h);
+        lx[i][ax] = make_float2(l, l);
       }
     }
-    for (int c = 0; c < nk && !S.abort; ++c) {
-      const int s = c % STAGES;
+    const float2 f2 = make_float2(factor, factor);
+    for (int c = 0; c < nk && !warp_aborted(S); ++c) {
+      const int s = c % STAGES, cs = c % kCS;
       const uint32_t ph = (c / STAGES) & 1;
-      if (c >= STAGES && !wait_or_abort(S, a.status, &S.empty[s], ph ^ 1)) break;
-      const int64_t q0 = (int64_t)c * KC + 8 * j;
-      float qh[8][3], ql[8][3];
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        if (ax < a.d) {
-          const float4 h0 = *reinterpret_cast<const float4 *>(a.ch + ax * a.npad + q0);
-          const float4 h1 = *reinterpret_cast<const float4 *>(a.ch + ax * a.npad + q0 + 4);
-          const float4 l0 = *reinterpret_cast<const float4 *>(a.cl + ax * a.npad + q0);
-          const float4 l1 = *reinterpret_cast<const float4 *>(a.cl + ax * a.npad + q0 + 4);
-          qh[0][ax] = h0.x; qh[1][ax] = h0.y; qh[2][ax] = h0.z; qh[3][ax] = h0.w;
-          qh[4][ax] = h1.x; qh[5][ax] = h1.y; qh[6][ax] = h1.z; qh[7][ax] = h1.w;
-          ql[0][ax] = l0.x; ql[1][ax] = l0.y; ql[2][ax] = l0.z; ql[3][ax] = l0.w;
-          ql[4][ax] = l1.x; ql[5][ax] = l1.y; ql[6][ax] = l1.z; ql[7][ax] = l1.w;
-        } else {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) qh[e][ax] = ql[e][ax] = 0.f;
-        }
-      }
-      // Column boxes of the 8 points (tag factoring only); usually one box.
-      int bq[8];
-      bool one_box = true;
-      if (TAGGED) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) bq[e] = a.box_of[min(q0 + e, a.n - 1)];
-        one_box = bq[0] == bq[7];
-      }
+      if (c >= STAGES && !warp_wait(S, a.status, &S.empty[s], ph ^ 1)) break;
+      if (!warp_wait(S, a.status, &S.cfull[cs], (c / kCS) & 1)) break;
       // A chunk that cannot meet the diagonal or the ragged edge needs no
       // per-entry checks (the test is uniform over the CTA).
-      const int64_t kc0 = (int64_t)c * KC;
-      const bool clean = (kc0 + KC <= row0 || kc0 >= row0 + MB) && kc0 + KC <= a.n &&
-                         row0 + MB <= a.n;
-      const float factor = entry_f32_factor<KERNEL>() * a.scale_a;
+      const int kc0 = c * KC;
+      const bool clean = (kc0 + KC <= (int)row0 || kc0 >= (int)row0 + MB) && kc0 + KC <= n32 &&
+                         (int)row0 + MB <= n32;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int r = rbase + 32 * i;
-        uint32_t hw[4], lw[4];
-        float w_row = factor;
-        if (TAGGED && one_box) w_row *= a.tau[(int64_t)brow[i] * a.b + bq[0]];
+        const int r = rbase + 32 * i, p = prow0 + 32 * i;
+        uint32_t pw[kParts][4];
 #pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-          float v2[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            float w = w_row;
-            if (TAGGED && !one_box) w = factor * a.tau[(int64_t)brow[i] * a.b + bq[e + u]];
-            float v = entry_f32_raw<KERNEL>(rh[i], rl[i], qh[e + u], ql[e + u]) * w;
-            if (!clean) {
-              const int64_t qq = q0 + e + u;
-              if (qq == prow[i] || qq >= a.n || prow[i] >= a.n) v = 0.f;
-            }
-            v2[u] = v;
+        for (int pr = 0; pr < 4; ++pr) {
+          const int P = 4 * j + pr;  // point pair within the chunk
+          const float4 q0 = S.qc[cs][0][pr][j], q1 = S.qc[cs][1][pr][j], q2 = S.qc[cs][2][pr][j];
+          const float2 dx = __fadd2_rn(__fadd2_rn(rx[i][0], make_float2(q0.x, q0.y)),
+                                       __fadd2_rn(lx[i][0], make_float2(q1.z, q1.w)));
+          const float2 dy = __fadd2_rn(__fadd2_rn(rx[i][1], make_float2(q0.z, q0.w)),
+                                       __fadd2_rn(lx[i][1], make_float2(q2.x, q2.y)));
+          float2 r2;
+          if (KERNEL == TBLR_KERNEL_LAPLACE3D) {
+            const float2 dz = __fadd2_rn(__fadd2_rn(rx[i][2], make_float2(q1.x, q1.y)),
+                                         __fadd2_rn(lx[i][2], make_float2(q2.z, q2.w)));
+            r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+          } else {
+            r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
           }
-          const __half2 h = __floats2half2_rn(v2[0], v2[1]);
-          const float2 hf = __half22float2(h);
-          const __half2 l = __floats2half2_rn(v2[0] - hf.x, v2[1] - hf.y);
-          hw[e / 2] = *reinterpret_cast<const uint32_t *>(&h);
-          lw[e / 2] = *reinterpret_cast<const uint32_t *>(&l);
+          const float2 e = make_float2(entry_f32_of_r2<KERNEL>(r2.x), entry_f32_of_r2<KERNEL>(r2.y));
+          float2 w = f2;
+          if (TAGGED) {
+            if (staged_w)
+              w = S.wt[cs][rbi[i]][pr][j];
+            else
+              w = make_float2(factor * a.tau[brow[i] + S.bq[cs][2 * P]],
+                              factor * a.tau[brow[i] + S.bq[cs][2 * P + 1]]);
+          }
+          float2 v = __fmul2_rn(e, w);
+          if (!clean) {
+            const int qq = kc0 + 2 * P;
+            if (qq == p || qq >= n32 || p >= n32) v.x = 0.f;
+            if (qq + 1 == p || qq + 1 >= n32 || p >= n32) v.y = 0.f;
+          }
+          split3(v.x, v.y, pw[0][pr], pw[1][pr], pw[2][pr]);
         }
         const int off = r * 128 + ((j ^ (r & 7)) << 4);  // 128-byte swizzle
-        *reinterpret_cast<uint4 *>(S.a[s][0] + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4 *>(S.a[s][1] + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+#pragma unroll
+        for (int t = 0; t < kParts; ++t)
+          *reinterpret_cast<uint4 *>(S.a[s][t] + off) =
+              make_uint4(pw[t][0], pw[t][1], pw[t][2], pw[t][3]);
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&S.full_a[s]);
+      if (lane == 0) {
+        tc::mbar_arrive(&S.cfree[cs]);
+        tc::mbar_arrive(&S.full_a[s]);
+      }
+    }
+  } else {
+    // -------------------------------------------------------------- stager
+    // Stages chunk c's point data into slot c % kCS as soon as the generators
+    // have released it (lane l takes points 2l, 2l + 1), so the generators
+    // never wait on global memory.
+    for (int c = 0; c < nk && !warp_aborted(S); ++c) {
+      const int cs = c % kCS;
+      if (c >= kCS && !warp_wait(S, a.status, &S.cfree[cs], ((c / kCS) & 1) ^ 1)) break;
+      const int64_t q = (int64_t)c * KC + 2 * lane;
+      float2 h[3], l[3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        h[ax] = ax < a.d ? *reinterpret_cast<const float2 *>(a.ch + ax * a.npad + q)
+                         : make_float2(0.f, 0.f);
+        l[ax] = ax < a.d ? *reinterpret_cast<const float2 *>(a.cl + ax * a.npad + q)
+                         : make_float2(0.f, 0.f);
+      }
+      const int pj = lane >> 2, pr = lane & 3;  // this lane's pair P = lane = 4 pj + pr
+      S.qc[cs][0][pr][pj] = make_float4(-h[0].x, -h[0].y, -h[1].x, -h[1].y);
+      S.qc[cs][1][pr][pj] = make_float4(-h[2].x, -h[2].y, -l[0].x, -l[0].y);
+      S.qc[cs][2][pr][pj] = make_float4(-l[1].x, -l[1].y, -l[2].x, -l[2].y);
+      if (TAGGED) {
+        const int b0 = a.box_of[min((int)q, n32 - 1)], b1 = a.box_of[min((int)q + 1, n32 - 1)];
+        S.bq[cs][2 * lane] = b0;
+        S.bq[cs][2 * lane + 1] = b1;
+        if (staged_w)
+          for (int rb = 0; rb < nrb; ++rb) {
+            const float *tr = a.tau + (int64_t)(rb0 + rb) * a.b;
+            S.wt[cs][rb][pr][pj] = make_float2(factor * tr[b0], factor * tr[b1]);
+          }
+      }
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&S.cfull[cs]);
     }
   }
 
@@ -369,20 +509,27 @@ __global__ void split_coords_kernel(const double *__restrict__ pts, int64_t n, i
   }
 }
 
-// X (FP64, K-major [ncols][n]) scaled by 2^4 and split into FP16 hi/lo planes
-// [ncols_pad][npad], zero padded.
+// Three-way BF16 split of an FP64 value (remainders exact in FP64), so
+// |x - h - m - l| <= 2^-24 |x|.
+__device__ __forceinline__ void split3_fp64(double x, __nv_bfloat16 &h, __nv_bfloat16 &m,
+                                            __nv_bfloat16 &l) {
+  h = __double2bfloat16(x);
+  const double r1 = x - (double)__bfloat162float(h);
+  m = __double2bfloat16(r1);
+  l = __double2bfloat16(r1 - (double)__bfloat162float(m));
+}
+
+// X (FP64, K-major [ncols][n]) split into BF16 h/m/l planes [ncols_pad][npad],
+// zero padded.
 __global__ void split_x_kernel(const double *__restrict__ xt, int64_t n, int64_t ncols,
-                               int64_t npad, int64_t ncols_pad, float scale,
-                               __half *__restrict__ xh, __half *__restrict__ xl) {
+                               int64_t npad, int64_t ncols_pad, __nv_bfloat16 *__restrict__ xh,
+                               __nv_bfloat16 *__restrict__ xm, __nv_bfloat16 *__restrict__ xl) {
   const int64_t total = npad * ncols_pad;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = i / npad, p = i % npad;
-    float v = 0.f;
-    if (c < ncols && p < n) v = (float)(xt[c * n + p] * (double)scale);
-    const __half h = __float2half_rn(v);
-    xh[i] = h;
-    xl[i] = __float2half_rn(v - __half2float(h));
+    const double v = (c < ncols && p < n) ? xt[c * n + p] : 0.0;
+    split3_fp64(v, xh[i], xm[i], xl[i]);
   }
 }
 
@@ -399,16 +546,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-int make_map(CUtensorMap *map, const __half *base, int64_t npad, int64_t rows, int box_rows) {
+int make_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t npad, int64_t rows,
+             int box_rows) {
   auto fn = encode_fn();
   TBLR_REQUIRE(fn != nullptr, "cuTensorMapEncodeTiled is unavailable");
   cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)npad * sizeof(__half)};
+  cuuint64_t strides[1] = {(cuuint64_t)npad * sizeof(__nv_bfloat16)};
   cuuint32_t box[2] = {KC, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half *>(base), dims, strides,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base),
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
     return TBLR_ECUDA;
@@ -416,7 +565,9 @@ int make_map(CUtensorMap *map, const __half *base, int64_t npad, int64_t rows, i
   return TBLR_OK;
 }
 
-// Column tiling of `ncols` outputs: tiles of equal width, a multiple of 32, at most 128.
+// Column tiling of `ncols` outputs: the fewest tiles of at most 160 columns,
+// of equal width rounded up to a multiple of 32 (the black-box apply uses
+// widths 128 and 160 only).
 struct ColTiles {
   int width, ntiles;
   int64_t padded;
@@ -424,13 +575,9 @@ struct ColTiles {
 
 ColTiles col_tiles(int64_t ncols, bool tagged) {
   ColTiles t;
-  if (!tagged) {
-    t.width = NB;
-    t.ntiles = (int)cdiv(ncols, NB);
-  } else {
-    t.ntiles = (int)cdiv(ncols, 128);
-    t.width = (int)(cdiv(cdiv(ncols, t.ntiles), 32) * 32);
-  }
+  t.ntiles = (int)cdiv(std::max<int64_t>(ncols, 1), kMaxNB);
+  t.width = (int)(cdiv(cdiv(std::max<int64_t>(ncols, 1), t.ntiles), 32) * 32);
+  if (!tagged) t.width = t.width <= 128 ? 128 : kMaxNB;
   t.padded = (int64_t)t.width * t.ntiles;
   return t;
 }
@@ -446,9 +593,9 @@ MixedLayout mixed_layout(const Prob &P, int64_t ncols, bool tagged) {
   L.ncols_pad = col_tiles(ncols, tagged).padded;
   L.head = 256;
   L.coords = align256(sizeof(float) * 2 * 3 * L.npad);
-  L.planes = align256(sizeof(__half) * L.npad * L.ncols_pad);
+  L.planes = align256(sizeof(__nv_bfloat16) * L.npad * L.ncols_pad);
   L.tau = tagged ? align256(sizeof(float) * P.b * P.b) : 0;
-  L.total = L.head + L.coords + 2 * L.planes + L.tau;
+  L.total = L.head + L.coords + kParts * L.planes + L.tau;
   return L;
 }
 
@@ -462,24 +609,22 @@ int env_flush() {
   return f;
 }
 
-// [G | H] gathered to box-major order, scaled by 2^4 and split into FP16 hi/lo
-// planes [ncols_pad][npad] (rows c < r from G, r <= c < 2r from H, zero padded).
+// [G | H] gathered to box-major order and split into BF16 h/m/l planes
+// [ncols_pad][npad] (rows c < r from G, r <= c < 2r from H, zero padded).
 __global__ void split_gh_kernel(const double *__restrict__ G, const double *__restrict__ H,
                                 const int32_t *__restrict__ perm, int64_t n, int r, int64_t npad,
-                                int64_t ncols_pad, float scale, __half *__restrict__ xh,
-                                __half *__restrict__ xl) {
+                                int64_t ncols_pad, __nv_bfloat16 *__restrict__ xh,
+                                __nv_bfloat16 *__restrict__ xm, __nv_bfloat16 *__restrict__ xl) {
   const int64_t total = npad * ncols_pad;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = i / npad, p = i % npad;
-    float v = 0.f;
+    double v = 0.0;
     if (p < n && c < 2 * r) {
       const int64_t src = (int64_t)perm[p] * r + (c < r ? c : c - r);
-      v = (float)((c < r ? G[src] : H[src]) * (double)scale);
+      v = c < r ? G[src] : H[src];
     }
-    const __half h = __float2half_rn(v);
-    xh[i] = h;
-    xl[i] = __float2half_rn(v - __half2float(h));
+    split3_fp64(v, xh[i], xm[i], xl[i]);
   }
 }
 
@@ -490,29 +635,29 @@ __global__ void tau_to_f32(const double *__restrict__ tau, int64_t len, float *_
 }
 
 template <int KERNEL, int NBT, bool TAGGED>
-int launch_mixed(const CUtensorMap &mh, const CUtensorMap &ml, const MixedArgs &a, int64_t n,
-                 int ntiles, cudaStream_t s) {
+int launch_mixed(const Maps &maps, const MixedArgs &a, int64_t n, int ntiles, cudaStream_t s) {
   auto k = mixed_apply_kernel<KERNEL, NBT, TAGGED>;
   const size_t smem = sizeof(Smem<NBT>) + 1024;
   TBLR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k<<<dim3((unsigned)cdiv(n, MB), (unsigned)ntiles), kThreads, smem, s>>>(mh, ml, a);
+  k<<<dim3((unsigned)cdiv(n, MB), (unsigned)ntiles), kThreads, smem, s>>>(maps, a);
   return launch_status("mixed_apply_kernel");
 }
 
 template <bool TAGGED>
-int dispatch_mixed(int kernel, int width, const CUtensorMap &mh, const CUtensorMap &ml,
-                   const MixedArgs &a, int64_t n, int ntiles, cudaStream_t s) {
-#define TBLR_MIXED_CASE(W)                                                                      \
-  if (width == W)                                                                               \
-    return kernel == TBLR_KERNEL_LAPLACE2D                                                      \
-               ? launch_mixed<TBLR_KERNEL_LAPLACE2D, W, TAGGED>(mh, ml, a, n, ntiles, s)        \
-               : launch_mixed<TBLR_KERNEL_LAPLACE3D, W, TAGGED>(mh, ml, a, n, ntiles, s);
-  if (TAGGED) {
+int dispatch_mixed(int kernel, int width, const Maps &maps, const MixedArgs &a, int64_t n,
+                   int ntiles, cudaStream_t s) {
+#define TBLR_MIXED_CASE(W)                                                                     \
+  if (width == W)                                                                              \
+    return kernel == TBLR_KERNEL_LAPLACE2D                                                     \
+               ? launch_mixed<TBLR_KERNEL_LAPLACE2D, W, TAGGED>(maps, a, n, ntiles, s)         \
+               : launch_mixed<TBLR_KERNEL_LAPLACE3D, W, TAGGED>(maps, a, n, ntiles, s);
+  if constexpr (TAGGED) {
     TBLR_MIXED_CASE(32)
     TBLR_MIXED_CASE(64)
     TBLR_MIXED_CASE(96)
   }
   TBLR_MIXED_CASE(128)
+  TBLR_MIXED_CASE(160)
 #undef TBLR_MIXED_CASE
   set_error("no tensor-core kernel for tile width %d", width);
   return TBLR_EUNSUPPORTED;
@@ -528,10 +673,26 @@ MixedArgs base_args(const Prob &P, const MixedLayout &L, float *ch, float *cl, v
   a.kernel = P.kernel;
   a.nk = (int)(L.npad / KC);
   a.flush = env_flush();
-  a.scale_a = P.kernel == TBLR_KERNEL_LAPLACE2D ? 16.f : 1.f;
-  a.unscale = 1.0 / ((double)a.scale_a * 16.0);
   a.status = status;
   return a;
+}
+
+// The three X planes of the workspace and their tensor maps.
+struct Planes {
+  __nv_bfloat16 *part[kParts];
+};
+
+Planes planes_of(char *w, const MixedLayout &L) {
+  Planes pl;
+  for (int t = 0; t < kParts; ++t)
+    pl.part[t] = reinterpret_cast<__nv_bfloat16 *>(w + L.head + L.coords + t * L.planes);
+  return pl;
+}
+
+int make_maps(Maps *maps, const Planes &pl, const MixedLayout &L, int width) {
+  for (int t = 0; t < kParts; ++t)
+    TBLR_TRY(make_map(&maps->part[t], pl.part[t], L.npad, L.ncols_pad, width));
+  return TBLR_OK;
 }
 
 }  // namespace
@@ -543,6 +704,7 @@ int apply_mixed(const Prob &P, const tblr_layout *lay, const double *xt, int64_t
                 int64_t ldy, void *ws, size_t ws_bytes, cudaStream_t s) {
   TBLR_REQUIRE(P.kernel == TBLR_KERNEL_LAPLACE2D || P.kernel == TBLR_KERNEL_LAPLACE3D,
                "mixed precision supports the built-in Laplace kernels");
+  TBLR_REQUIRE(P.n < (int64_t)1 << 30, "mixed precision supports n < 2^30 points");
   const MixedLayout L = mixed_layout(P, ncols, false);
   TBLR_REQUIRE(ws != nullptr && ws_bytes >= L.total, "mixed workspace too small (%zu < %zu)",
                ws_bytes, L.total);
@@ -551,19 +713,17 @@ int apply_mixed(const Prob &P, const tblr_layout *lay, const double *xt, int64_t
   int *status = reinterpret_cast<int *>(w);
   float *ch = reinterpret_cast<float *>(w + L.head);
   float *cl = ch + 3 * L.npad;
-  __half *xh = reinterpret_cast<__half *>(w + L.head + L.coords);
-  __half *xl = reinterpret_cast<__half *>(w + L.head + L.coords + L.planes);
+  const Planes pl = planes_of(w, L);
   TBLR_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
   split_coords_kernel<<<(unsigned)std::min<int64_t>(cdiv(3 * L.npad, 256), 4096), 256, 0, s>>>(
       lay->pts, P.n, L.npad, P.d, ch, cl);
   TBLR_TRY(launch_status("split_coords_kernel"));
   split_x_kernel<<<(unsigned)std::min<int64_t>(cdiv(L.npad * L.ncols_pad, 256), 152 * 32), 256, 0,
-                   s>>>(xt, P.n, ncols, L.npad, L.ncols_pad, 16.f, xh, xl);
+                   s>>>(xt, P.n, ncols, L.npad, L.ncols_pad, pl.part[0], pl.part[1], pl.part[2]);
   TBLR_TRY(launch_status("split_x_kernel"));
   const ColTiles ct = col_tiles(ncols, false);
-  CUtensorMap mh, ml;
-  TBLR_TRY(make_map(&mh, xh, L.npad, L.ncols_pad, ct.width));
-  TBLR_TRY(make_map(&ml, xl, L.npad, L.ncols_pad, ct.width));
+  Maps maps;
+  TBLR_TRY(make_maps(&maps, pl, L, ct.width));
   MixedArgs a = base_args(P, L, ch, cl, status);
   a.ncols = ncols;
   a.ldy = ldy;
@@ -571,7 +731,7 @@ int apply_mixed(const Prob &P, const tblr_layout *lay, const double *xt, int64_t
   a.split = ncols;
   a.ldy2 = 0;
   a.y2 = nullptr;
-  return dispatch_mixed<false>(P.kernel, ct.width, mh, ml, a, P.n, ct.ntiles, s);
+  return dispatch_mixed<false>(P.kernel, ct.width, maps, a, P.n, ct.ntiles, s);
 }
 
 int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau, const double *G,
@@ -579,6 +739,8 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
                         cudaStream_t s) {
   TBLR_REQUIRE(P.kernel == TBLR_KERNEL_LAPLACE2D || P.kernel == TBLR_KERNEL_LAPLACE3D,
                "mixed precision supports the built-in Laplace kernels");
+  TBLR_REQUIRE(P.n < (int64_t)1 << 30, "mixed precision supports n < 2^30 points");
+  TBLR_REQUIRE(P.b * P.b < (int64_t)1 << 31, "too many boxes for the tag table");
   const int64_t ncols = 2 * P.r;
   const MixedLayout L = mixed_layout(P, ncols, true);
   TBLR_REQUIRE(ws != nullptr && ws_bytes >= L.total, "tagged sketch workspace too small");
@@ -587,23 +749,22 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
   int *status = reinterpret_cast<int *>(w);
   float *ch = reinterpret_cast<float *>(w + L.head);
   float *cl = ch + 3 * L.npad;
-  __half *xh = reinterpret_cast<__half *>(w + L.head + L.coords);
-  __half *xl = reinterpret_cast<__half *>(w + L.head + L.coords + L.planes);
-  float *tf = reinterpret_cast<float *>(w + L.head + L.coords + 2 * L.planes);
+  const Planes pl = planes_of(w, L);
+  float *tf = reinterpret_cast<float *>(w + L.head + L.coords + kParts * L.planes);
   TBLR_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
   split_coords_kernel<<<(unsigned)std::min<int64_t>(cdiv(3 * L.npad, 256), 4096), 256, 0, s>>>(
       lay->pts, P.n, L.npad, P.d, ch, cl);
   TBLR_TRY(launch_status("split_coords_kernel"));
   split_gh_kernel<<<(unsigned)std::min<int64_t>(cdiv(L.npad * L.ncols_pad, 256), 152 * 32), 256, 0,
-                    s>>>(G, H, lay->perm, P.n, P.r, L.npad, L.ncols_pad, 16.f, xh, xl);
+                    s>>>(G, H, lay->perm, P.n, P.r, L.npad, L.ncols_pad, pl.part[0], pl.part[1],
+                         pl.part[2]);
   TBLR_TRY(launch_status("split_gh_kernel"));
   tau_to_f32<<<(unsigned)std::min<int64_t>(cdiv(P.b * P.b, 256), 1024), 256, 0, s>>>(tau, P.b * P.b,
                                                                                      tf);
   TBLR_TRY(launch_status("tau_to_f32"));
   const ColTiles ct = col_tiles(ncols, true);
-  CUtensorMap mh, ml;
-  TBLR_TRY(make_map(&mh, xh, L.npad, L.ncols_pad, ct.width));
-  TBLR_TRY(make_map(&ml, xl, L.npad, L.ncols_pad, ct.width));
+  Maps maps;
+  TBLR_TRY(make_maps(&maps, pl, L, ct.width));
   MixedArgs a = base_args(P, L, ch, cl, status);
   a.ncols = ncols;
   a.ldy = P.r;
@@ -614,7 +775,7 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
   a.tau = tf;
   a.box_of = lay->box_of;
   a.b = (int)P.b;
-  return dispatch_mixed<true>(P.kernel, ct.width, mh, ml, a, P.n, ct.ntiles, s);
+  return dispatch_mixed<true>(P.kernel, ct.width, maps, a, P.n, ct.ntiles, s);
 }
 
 }  // namespace tblr

@@ -1,4 +1,4 @@
-// Mixed-precision black-box apply (split FP16 operands on tcgen05 tensor cores,
+// Mixed-precision black-box apply (three-part BF16 operands on tcgen05 tensor cores,
 // FP32 accumulation in TMEM); see mixed.cu.
 #pragma once
 #include "common.cuh"

@@ -123,6 +123,65 @@ __device__ __forceinline__ void jacobi_pair(int rho, int k, int qq, int *a, int 
   }
 }
 
+// One-sided (Hestenes) Jacobi on the q columns (length r, column a at
+// B[a * r]) of B, accumulating the rotations in the q x q matrix X (column a at
+// X[a * q]); round-robin pair schedule, one warp per pair, sweeps until no
+// pair has |gamma| > tol sqrt(alpha beta) or `max_sweeps` is reached.
+template <class T>
+__device__ void jacobi_sweeps(T *B, T *X, int q, int r, T tol, int max_sweeps, int *rotated) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nw = kColThreads / 32;
+  const int qq = q + (q & 1);
+  if (tid == 0) *rotated = 0;
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int rho = 0; rho < qq - 1; ++rho) {
+      for (int pr = warp; pr < qq / 2; pr += nw) {
+        int a, bb;
+        jacobi_pair(rho, pr, qq, &a, &bb);
+        if (a >= q || bb >= q) continue;
+        if (a > bb) {
+          const int tt = a;
+          a = bb;
+          bb = tt;
+        }
+        T al = 0, be = 0, ga = 0;
+        for (int c = lane; c < r; c += 32) {
+          const T x = B[a * r + c], y = B[bb * r + c];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != T(0) && fabs(ga) > tol * sqrt(al * be)) {
+          const T zeta = (be - al) / (T(2) * ga);
+          const T tn = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T cs = T(1) / sqrt(T(1) + tn * tn), sn = cs * tn;
+          for (int c = lane; c < r; c += 32) {
+            const T x = B[a * r + c], y = B[bb * r + c];
+            B[a * r + c] = cs * x - sn * y;
+            B[bb * r + c] = sn * x + cs * y;
+          }
+          for (int c = lane; c < q; c += 32) {
+            const T x = X[a * q + c], y = X[bb * q + c];
+            X[a * q + c] = cs * x - sn * y;
+            X[bb * q + c] = sn * x + cs * y;
+          }
+          if (lane == 0) *rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = *rotated;
+    __syncthreads();
+    if (!any) break;
+    if (tid == 0) *rotated = 0;
+    __syncthreads();
+  }
+}
+
 struct ColArgs {
   const double *S;
   double *U;
@@ -201,66 +260,75 @@ __global__ void __launch_bounds__(kColThreads) col_kernel(ColArgs A) {
     __syncthreads();
   }
 
-  // B = R^T (r x q, column a = row a of R), X = I.
-  for (int idx = tid; idx < q * r; idx += kColThreads) {
-    const int a = idx / r, c = idx % r;
-    B[idx] = (c >= a) ? W[(int64_t)c * m + a] : 0.0;
+  // SVD of R through one-sided Jacobi on B = R^T (column a of B = row a of
+  // R): R^T X = B with orthogonal columns, so R = X diag(|B_a|) (B_a/|B_a|)^T
+  // and the columns of X are R's left singular vectors.  GB300's FP64 pipe is
+  // ~60x slower than FP32, so the sweeps first run in FP32 (in the same
+  // shared memory), then B = R^T X is formed in FP64 from the FP32 rotations
+  // and FP64 sweeps polish it from that nearly orthogonal start (quadratic
+  // convergence: typically one rotating sweep and one that confirms).
+  {
+    float *Bf = reinterpret_cast<float *>(B);
+    float *Xf = reinterpret_cast<float *>(X);
+    for (int idx = tid; idx < q * r; idx += kColThreads) {
+      const int a = idx / r, c = idx % r;
+      Bf[idx] = (c >= a) ? (float)W[(int64_t)c * m + a] : 0.f;
+    }
+    for (int idx = tid; idx < q * q; idx += kColThreads) Xf[idx] = (idx / q == idx % q) ? 1.f : 0.f;
+    __syncthreads();
+    jacobi_sweeps<float>(Bf, Xf, q, r, 4.f * r * 1.1920929e-7f, 30, &rotated);
+    // Widen X: park the FP32 rotations in the free upper half of B's space
+    // (Bf uses the lower half; q <= r), then write them back as FP64.
+    float *Xp = Bf + q * r;
+    for (int idx = tid; idx < q * q; idx += kColThreads) Xp[idx] = Xf[idx];
+    __syncthreads();
+    for (int idx = tid; idx < q * q; idx += kColThreads) X[idx] = (double)Xp[idx];
+    __syncthreads();
   }
-  for (int idx = tid; idx < q * q; idx += kColThreads) X[idx] = (idx / q == idx % q) ? 1.0 : 0.0;
-  if (tid == 0) rotated = 0;
-  __syncthreads();
-
-  // One-sided (Hestenes) Jacobi on the columns of R^T: R^T X = B with
-  // orthogonal columns, so R = X diag(|B_a|) (B_a/|B_a|)^T and the columns of
-  // X are R's left singular vectors.
-  const int qq = q + (q & 1);
-  const double tol = 1e-15;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    for (int rho = 0; rho < qq - 1; ++rho) {
-      for (int pr = warp; pr < qq / 2; pr += nw) {
-        int a, bb;
-        jacobi_pair(rho, pr, qq, &a, &bb);
-        if (a >= q || bb >= q) continue;
-        if (a > bb) {
-          const int tt = a;
-          a = bb;
-          bb = tt;
+  // The FP32 rotations are orthogonal to ~1e-6 only and rotations cannot fix
+  // that, so re-orthonormalise X's columns in FP64 (classical Gram-Schmidt,
+  // twice per column; the projections of a column use the Bf space as
+  // scratch).
+  {
+    double *proj = reinterpret_cast<double *>(B);  // [q] coefficients
+    for (int a = 0; a < q; ++a) {
+      double *xa = X + a * q;
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int bcol = warp; bcol < a; bcol += nw) {
+          double d = 0.0;
+          for (int c = lane; c < q; c += 32) d += X[bcol * q + c] * xa[c];
+          d = warp_sum(d);
+          if (lane == 0) proj[bcol] = d;
         }
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int c = lane; c < r; c += 32) {
-          const double x = B[a * r + c], y = B[bb * r + c];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
+        __syncthreads();
+        for (int c = tid; c < q; c += kColThreads) {
+          double v = xa[c];
+          for (int bcol = 0; bcol < a; ++bcol) v -= proj[bcol] * X[bcol * q + c];
+          xa[c] = v;
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double tn = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + tn * tn), sn = cs * tn;
-          for (int c = lane; c < r; c += 32) {
-            const double x = B[a * r + c], y = B[bb * r + c];
-            B[a * r + c] = cs * x - sn * y;
-            B[bb * r + c] = sn * x + cs * y;
-          }
-          for (int c = lane; c < q; c += 32) {
-            const double x = X[a * q + c], y = X[bb * q + c];
-            X[a * q + c] = cs * x - sn * y;
-            X[bb * q + c] = sn * x + cs * y;
-          }
-          if (lane == 0) rotated = 1;
-        }
+        __syncthreads();
+      }
+      if (warp == 0) {
+        double nn = 0.0;
+        for (int c = lane; c < q; c += 32) nn += xa[c] * xa[c];
+        nn = warp_sum(nn);
+        if (lane == 0) proj[q] = 1.0 / sqrt(nn);
       }
       __syncthreads();
+      for (int c = tid; c < q; c += kColThreads) xa[c] *= proj[q];
+      __syncthreads();
     }
-    const int any = rotated;
-    __syncthreads();
-    if (!any) break;
-    if (tid == 0) rotated = 0;
-    __syncthreads();
   }
+  // B = R^T X in FP64 (R upper triangular: R(t, c) = W[c m + t], t <= c).
+  for (int idx = tid; idx < q * r; idx += kColThreads) {
+    const int a = idx / r, c = idx % r;
+    const int tmax = min(c, q - 1);
+    double acc = 0.0;
+    for (int t = 0; t <= tmax; ++t) acc += W[(int64_t)c * m + t] * X[a * q + t];
+    B[idx] = acc;
+  }
+  __syncthreads();
+  jacobi_sweeps<double>(B, X, q, r, 4.0 * r * 2.220446049250313e-16, 12, &rotated);
 
   // Singular values and their descending order (ties: lower index first).
   for (int a = warp; a < q; a += nw) {

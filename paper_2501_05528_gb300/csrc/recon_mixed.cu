@@ -208,63 +208,98 @@ __device__ int probe_set_f(int j, int mode, const int32_t *__restrict__ colour, 
   return cnt;
 }
 
-// CTA per (i, s, 64-column tile of M): M_is(a, q) for a < k, q in the tile.
-// Each set member c contributes Atilde_ic V_c(q, :)^T; that contribution is
-// summed in FP32 and added to Kahan sums.
-constexpr int kQT = 64;
+// CTA per (i, s, 128-column tile of M): M_is(a, q) for a < k, q in the tile.
+// Each set member c contributes Atilde_ic V_c(q, :)^T: Atilde_ic^T and the
+// tile's columns of V_c^T are staged in shared memory (t-major, so a thread
+// reads its 4 rows and 8 columns with three 16-byte loads per rank index t),
+// each thread accumulates a 4 x 8 block over 16 rank indices at a time and
+// adds it to Kahan sums.
+constexpr int kQT = 128;     // columns of M per CTA
+constexpr int kAS = 64 + 4;  // row stride of Atilde^T in shared memory (k <= 64)
+constexpr int kVS = kQT + 4;  // row stride of V^T in shared memory
 __global__ void __launch_bounds__(kThreads) nf_lowrank_f32_kernel(
     const int32_t *__restrict__ offsets, const int32_t *__restrict__ nbr,
     const int32_t *__restrict__ nnbr, const int32_t *__restrict__ colour, int b, int s3, int k,
-    int mmax, int mode, const double *__restrict__ At, const double *__restrict__ V,
+    int mmax, int mode, const double *__restrict__ At, const float *__restrict__ vt, int64_t n,
     float *__restrict__ M) {
-  extern __shared__ float sf[];
+  extern __shared__ __align__(16) float sf[];
   const int i = blockIdx.x, s = blockIdx.y, q0 = blockIdx.z * kQT, tid = threadIdx.x;
   if (s >= nnbr[i]) return;
   const int j = nbr[(int64_t)i * s3 + s];
   const int mj = offsets[j + 1] - offsets[j];
   if (q0 >= mj) return;
-  float *As = sf;                 // [k][k]
-  float *Vs = As + k * k;         // [kQT][k + 1]
-  int *set = reinterpret_cast<int *>(Vs + kQT * (k + 1));
+  float *As = sf;               // [64][kAS]: As[t * kAS + a] = Atilde_ic(a, t)
+  float *Vs = As + 64 * kAS;    // [64][kVS]: Vs[t * kVS + q] = V_c(q0 + q, t)
+  int *set = reinterpret_cast<int *>(Vs + 64 * kVS);
   const int ns = probe_set_f(j, mode, colour, b, set);
-  const int q = tid % kQT, ag = tid / kQT;  // 4 groups of rows a = ag + 4 u
-  constexpr int kU = 16;                    // k <= 64
-  float hi[kU], cc[kU];
+  for (int idx = tid; idx < 64 * kAS; idx += kThreads) As[idx] = 0.f;  // rows a >= k stay 0
+  const int ta = tid % 16, tq = tid / 16;  // rows 4 ta + x, columns 8 tq + y
+  float hi[4][8], cc[4][8];
 #pragma unroll
-  for (int u = 0; u < kU; ++u) hi[u] = cc[u] = 0.f;
-  for (int x = 0; x < ns; ++x) {
-    const int c = set[x];
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 8; ++y) hi[x][y] = cc[x][y] = 0.f;
+  for (int u = 0; u < ns; ++u) {
+    const int c = set[u];
     const int oc = offsets[c], mc = offsets[c + 1] - oc;
+    if (q0 >= mc) continue;  // uniform over the CTA
+    const int qn = min(min(mc, mj) - q0, kQT);
     __syncthreads();
-    for (int idx = tid; idx < k * k; idx += kThreads)
-      As[idx] = (float)At[((int64_t)i * b + c) * k * k + idx];
-    for (int idx = tid; idx < kQT * k; idx += kThreads) {
-      const int qq = idx / k, t = idx % k;
-      Vs[qq * (k + 1) + t] = (q0 + qq < mc && q0 + qq < mj) ? (float)V[((int64_t)oc + q0 + qq) * k + t]
-                                                             : 0.f;
+    const double *Ac = At + ((int64_t)i * b + c) * k * k;
+    for (int idx = tid; idx < k * k; idx += kThreads) {
+      const int a = idx / k, t = idx % k;
+      As[t * kAS + a] = (float)Ac[idx];
+    }
+    for (int idx = tid; idx < k * kQT; idx += kThreads) {
+      const int t = idx / kQT, q = idx % kQT;
+      Vs[t * kVS + q] = q < qn ? vt[(int64_t)t * n + oc + q0 + q] : 0.f;
     }
     __syncthreads();
-    float acc[kU];
+    for (int t0 = 0; t0 < k; t0 += 16) {
+      float acc[4][8];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) acc[u] = 0.f;
-    for (int t = 0; t < k; ++t) {
-      const float vq = Vs[q * (k + 1) + t];
+      for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int a = ag + 4 * u;
-        if (a < k) acc[u] = fmaf(As[a * k + t], vq, acc[u]);
+        for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+      const int t1 = min(t0 + 16, k);
+      for (int t = t0; t < t1; ++t) {
+        const float4 av = *reinterpret_cast<const float4 *>(As + t * kAS + 4 * ta);
+        const float4 v0 = *reinterpret_cast<const float4 *>(Vs + t * kVS + 8 * tq);
+        const float4 v1 = *reinterpret_cast<const float4 *>(Vs + t * kVS + 8 * tq + 4);
+        const float ar[4] = {av.x, av.y, av.z, av.w};
+        const float vr[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(ar[x], vr[y], acc[x][y]);
       }
-    }
 #pragma unroll
-    for (int u = 0; u < kU; ++u) kahan_add(hi[u], cc[u], acc[u]);
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) kahan_add(hi[x][y], cc[x][y], acc[x][y]);
+    }
   }
-  if (q0 + q < mj) {
-    float *out = M + ((int64_t)i * s3 + s) * k * mmax;
+  float *out = M + ((int64_t)i * s3 + s) * k * mmax;
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int a = ag + 4 * u;
-      if (a < k) out[(int64_t)a * mmax + q0 + q] = hi[u] - cc[u];
+  for (int x = 0; x < 4; ++x) {
+    const int a = 4 * ta + x;
+    if (a >= k) continue;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      const int q = q0 + 8 * tq + y;
+      if (q < mj) out[(int64_t)a * mmax + q] = hi[x][y] - cc[x][y];
     }
+  }
+}
+
+// V (FP64, n x k row-major) as FP32 V^T (k x n), the layout nf_lowrank reads.
+__global__ void transpose_v_f32(const double *__restrict__ v, int64_t n, int k,
+                                float *__restrict__ vt) {
+  const int64_t total = n * k;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = idx / n, p = idx % n;
+    vt[idx] = (float)v[p * k + t];
   }
 }
 
@@ -349,21 +384,30 @@ __global__ void __launch_bounds__(kThreads) nf_block_f32_kernel(
     }
   }
   __syncthreads();
-  float lr[4][4];
-#pragma unroll
-  for (int x = 0; x < 4; ++x)
-#pragma unroll
-    for (int y = 0; y < 4; ++y) lr[x][y] = 0.f;
-  for (int a = 0; a < k; ++a) {
-    float uu[4], mm[4];
-#pragma unroll
-    for (int x = 0; x < 4; ++x) uu[x] = Us[(4 * ty + x) * (k + 1) + a];
-#pragma unroll
-    for (int y = 0; y < 4; ++y) mm[y] = Ms[a * (kBT + 4) + 4 * tx + y];
+  // Low-rank part U_i M_is, subtracted from the Kahan sums 8 rank terms at a
+  // time (so each FP32 partial sum has at most 8 roundings).
+  for (int a0 = 0; a0 < k; a0 += 8) {
+    float lr[4][4];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) lr[x][y] = fmaf(uu[x], mm[y], lr[x][y]);
+      for (int y = 0; y < 4; ++y) lr[x][y] = 0.f;
+    const int a1 = min(a0 + 8, k);
+    for (int a = a0; a < a1; ++a) {
+      float uu[4], mm[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) uu[x] = Us[(4 * ty + x) * (k + 1) + a];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) mm[y] = Ms[a * (kBT + 4) + 4 * tx + y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) lr[x][y] = fmaf(uu[x], mm[y], lr[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) kahan_add(hi[x][y], cc[x][y], -lr[x][y]);
   }
   double *out = Bn + nf_off[(int64_t)i * s3 + s];
 #pragma unroll
@@ -373,8 +417,7 @@ __global__ void __launch_bounds__(kThreads) nf_block_f32_kernel(
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
       const int q = q0 + 4 * tx + y;
-      if (q < mj)
-        out[(int64_t)p * mj + q] = ((double)hi[x][y] - (double)cc[x][y]) - (double)lr[x][y];
+      if (q < mj) out[(int64_t)p * mj + q] = (double)hi[x][y] - (double)cc[x][y];
     }
   }
 }
@@ -425,7 +468,7 @@ int coupling_mixed(const Prob &P, const tblr_layout *lay, const double *u, const
 size_t nearfield_mixed_workspace(const Prob &P, int mmax) {
   const int64_t npad = cdiv(P.n, 64) * 64;
   return align256(sizeof(float) * P.b * P.s3 * P.k * (size_t)mmax) +
-         2 * align256(sizeof(float) * 3 * npad);
+         2 * align256(sizeof(float) * 3 * npad) + align256(sizeof(float) * P.n * P.k);
 }
 
 int nearfield_mixed(const Prob &P, const tblr_layout *lay, const double *u, const double *at,
@@ -438,16 +481,21 @@ int nearfield_mixed(const Prob &P, const tblr_layout *lay, const double *u, cons
   float *ch = reinterpret_cast<float *>(w + align256(sizeof(float) * P.b * P.s3 * P.k * (size_t)mmax));
   float *cl = reinterpret_cast<float *>(reinterpret_cast<char *>(ch) +
                                         align256(sizeof(float) * 3 * npad));
+  float *vt = reinterpret_cast<float *>(reinterpret_cast<char *>(cl) +
+                                       align256(sizeof(float) * 3 * npad));
   split_all_coords<<<(unsigned)std::min<int64_t>(cdiv(3 * npad, 256), 4096), 256, 0, s>>>(
       lay->pts, P.n, npad, P.d, ch, cl);
   TBLR_TRY(launch_status("split_all_coords"));
-  const size_t smem_lr = sizeof(float) * (P.k * P.k + kQT * (P.k + 1)) + sizeof(int) * P.b;
+  transpose_v_f32<<<(unsigned)std::min<int64_t>(cdiv(P.n * P.k, 256), 152 * 16), 256, 0, s>>>(
+      v, P.n, P.k, vt);
+  TBLR_TRY(launch_status("transpose_v_f32"));
+  const size_t smem_lr = sizeof(float) * 64 * (kAS + kVS) + sizeof(int) * P.b;
   TBLR_REQUIRE(smem_lr <= 220 * 1024, "mixed near field: too many boxes for the probe set");
   TBLR_CUDA(cudaFuncSetAttribute(nf_lowrank_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_lr));
   nf_lowrank_f32_kernel<<<dim3((unsigned)P.b, (unsigned)P.s3, (unsigned)cdiv(mmax, kQT)), kThreads,
                           smem_lr, s>>>(lay->offsets, lay->nbr, lay->nnbr, lay->colour, (int)P.b,
-                                        P.s3, P.k, mmax, P.nearfield, at, v, M);
+                                        P.s3, P.k, mmax, P.nearfield, at, vt, P.n, M);
   TBLR_TRY(launch_status("nf_lowrank_f32_kernel"));
   const size_t smem_b = sizeof(float) * (kBT * (P.k + 1) + P.k * (kBT + 4) + 6 * kBT) +
                         sizeof(int) * P.b;

@@ -1,11 +1,12 @@
-"""GPU parity of the mixed-precision (tcgen05, split FP16, FP32 accumulation) path.
+"""GPU parity of the mixed-precision (tcgen05, three-part BF16, FP32 accumulation) path.
 
 Bound: the split-precision apply and the whole compression built on it must
 match the FP64 oracle within 1e-6 relative Frobenius error (the stated bound
-for the mixed path).  The dropped lo*lo term contributes ~2^-22, FP16
-rounding of each half ~2^-23 relative per product, and the FP32 tensor-core
-accumulation is flushed every 64 points into compensated sums, so the measured
-error is expected near 1e-7.  Cases have ragged row and column tails.
+for the mixed path).  Each operand is carried as three BF16 parts (2^-24
+relative), the dropped products are <= 2^-24, FP32 kernel entries are within
+~1 ulp, and the FP32 tensor-core accumulation is flushed every 64 points into
+compensated sums, so a sketch is expected near 1e-7.  Cases have ragged row
+and column tails and cover every tile width of the tensor-core kernel.
 """
 import numpy as np
 import pytest
@@ -83,3 +84,45 @@ def test_mixed_compression_within_bound(kind, d, grid, n, k, e, sketch):
     err = metrics.ublr_difference(off, nbr, cnt, s3, ref["ranks"], rep, rep_o)
     print(f"mixed compression {kind} n={n} sketch={sketch}: rel err vs FP64 oracle {err:.3e}")
     assert err < MIXED_BOUND
+
+
+# 2r = 22, 60, 90, 120, 148 sketch columns: tile widths 32, 64, 96, 128 and 160
+@pytest.mark.parametrize("kind,d,grid,n,k", [("laplace2d", 2, (4, 4), 1900, 1),
+                                            ("laplace3d", 3, (3, 3, 3), 2100, 20),
+                                            ("laplace2d", 2, (5, 4), 2750, 35),
+                                            ("laplace3d", 3, (3, 3, 2), 2900, 50),
+                                            ("laplace2d", 2, (3, 3), 3100, 64)])
+def test_mixed_tagged_sketch_every_tile_width(kind, d, grid, n, k):
+    """S_i = sum_c tau_i(c) A(I_i, I_c) G(I_c) and R_j = sum_c tau_j(c) A(I_c, I_j)^T H(I_c)
+    (the tag-factored form of the combination S_i = sum_j z_ij Y_j of §5.3), written out
+    densely here from the oracle's tessellation and projected tags."""
+    tb = _tb()
+    r = k + 10
+    pts = inputs.uniform_points(n, d, seed=11 * n)
+    lo, hi = (0.0,) * d, (1.0,) * d
+    b = int(np.prod(grid))
+    ell = orc.tag_columns(d, 3)
+    T, G, H = inputs.tagging_draws(b, ell, n, r, seed=11 * n + 1)
+    tess = orc.tessellate(pts, grid, lo, hi)
+    _, tau, _ = orc.decode(T, tess)
+    perm = tess["perm"]
+    box = np.repeat(np.arange(b), np.diff(tess["offsets"]))
+    A = orc.dense_matrix(orc.KernelOperator(kind, pts[perm]))
+    W = tau[box[:, None], box[None, :]]
+    S_ref = (A * W) @ G[perm]
+    R_ref = (A.T * W) @ H[perm]   # row p of R: sum_q tau_{box p}(box q) A(q, p) H(q)
+    prob = tb.make_problem(d, kind, n, grid, lo, hi, k, 10, 3, precision=tb.MIXED,
+                           sketch=tb.SKETCH_TAGGED)
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    lay = tb.tblr_tessellate(prob, t(pts))
+    assert np.array_equal(lay.perm.cpu().numpy(), perm)
+    s, rr = tb.tblr_tagged_sketch(prob, lay, t(tau), t(G), t(H))
+    s, rr = s.cpu().numpy(), rr.cpu().numpy()
+    assert tb.tblr_device_timeouts() == 0
+    for got, ref in ((s, S_ref), (rr, R_ref)):
+        err = metrics.rel(got, ref)
+        print(f"mixed tagged sketch {kind} n={n} 2r={2 * r}: rel err {err:.3e}")
+        assert err < MIXED_BOUND / 4
+        row_err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert row_err.max() < MIXED_BOUND
