@@ -51,15 +51,14 @@ constexpr int kMaxNB = 160;
 constexpr int kParts = 3;  // BF16 parts per operand value
 constexpr int kGenWarps = 8;
 constexpr int kEpiWarps = 4;
-constexpr int kStageWarp = 2 + kEpiWarps + kGenWarps;  // stages point data
-constexpr int kThreads = 32 * (kStageWarp + 1);
+constexpr int kThreads = 32 * (2 + kEpiWarps + kGenWarps);
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitBudget = 1000000000LL;  // clock cycles (~0.5 s) per wait
 constexpr int kTileBytes = MB * 128;             // one BF16 part of an A tile
 constexpr int kSmemLimit = 232448;               // 227 KiB of opt-in shared memory per CTA
-constexpr int kCS = 3;      // slots of staged point data (the producer runs kCS - 1 chunks ahead)
-constexpr int kMaxRB = 4;   // row boxes per CTA with staged tag weights (else gathered)
-constexpr int kCoordBytes = kCS * (KC / 2 * 12 * 4 + kMaxRB * KC * 4 + KC * 4);
+constexpr int kCS = 3;      // slots of staged point data (copied kCS - 1 chunks ahead)
+constexpr int kQcBytes = KC / 2 * 12 * 4;  // one chunk's staged coordinates
+constexpr int kCoordBytes = kCS * (kQcBytes + KC * 4);
 
 // Shared-memory stages and TMEM accumulators for an NBT-column tile.  The
 // tile's columns are accumulated in H units of UC = NBT / H columns; units
@@ -75,6 +74,9 @@ struct Cfg {
   static_assert(NBT % 32 == 0 && NBT <= kMaxNB, "tile width");
   static_assert(UC % 16 == 0 && (UC * 128) % 1024 == 0, "unit width");
   static_assert(STAGES * kStageBytes + kCoordBytes + 2048 <= kSmemLimit, "shared memory");
+  // Room left for the tag rows tau(row box, :) of the tile's row boxes.
+  static constexpr int kTauFloats =
+      ((kSmemLimit - 2048 - STAGES * kStageBytes - kCoordBytes) / 4) & ~3;
   static_assert(2 * UC + 2 * NBT <= (int)kTmemCols, "tensor memory");
 };
 
@@ -83,16 +85,15 @@ struct __align__(1024) Smem {
   static constexpr int STAGES = Cfg<NBT>::STAGES;
   uint8_t a[STAGES][kParts][kTileBytes];  // A h, m, l: 128 rows x 128 bytes
   uint8_t x[STAGES][kParts][NBT * 128];   // X h, m, l: NBT rows x 128 bytes
-  // Point data of a chunk, staged by the producer warp.  Point pair
-  // P = 4 j + pr (points 2P, 2P + 1) sits at [pr][j], so the 8 pairs a warp
-  // reads at once are 8 consecutive 16-byte (or 8-byte) words: no bank
-  // conflicts.  qc: negated coordinates as three float4 fields
-  // {xh, yh}, {zh, xl}, {yl, zl} (each a pair of the two points); wt: the
-  // kernel factor times the tag weight per row box and pair; bq: the column
-  // box of each point.
+  // Point data of a chunk, bulk-copied by the producer from the staged
+  // layout (one 1.5 KiB block per chunk): point pair P = 4 j + pr (points
+  // 2P, 2P + 1) sits at [f][pr][j], so the 8 pairs a warp reads at once are 8
+  // consecutive 16-byte words (no bank conflicts); the three float4 fields f
+  // hold the negated coordinates {xh, yh}, {zh, xl}, {yl, zl} of the pair.
+  // bq: the column box of each point (tag factoring).
   float4 qc[kCS][3][4][8];
-  float2 wt[kCS][kMaxRB][4][8];
   int bq[kCS][KC];
+  float taus[Cfg<NBT>::kTauFloats];  // tau rows of the tile's row boxes
   uint64_t cfull[kCS], cfree[kCS];
   uint64_t full_a[STAGES], full_b[STAGES], empty[STAGES];
   uint64_t dfull[2], dempty[2], done;
@@ -105,7 +106,8 @@ struct Maps {
 };
 
 struct MixedArgs {
-  const float *ch, *cl;  // coordinates, hi and lo floats, [d][npad]
+  const float4 *qst;     // staged coordinates, [npad / 64][3][4][8] (see Smem::qc)
+  const int32_t *boxpad; // box of each point, padded to npad with the last box
   int64_t n, npad;
   int d, kernel, nk, flush;
   int64_t ncols, ldy;
@@ -209,21 +211,35 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::fence_mbar_init();
     for (int t = 0; t < kParts; ++t) tc::tma_prefetch(&maps.part[t]);
   }
+  // Boxes of this tile's rows (rows are box-major, so they form a range) and
+  // their tag rows tau(row box, :) in shared memory when they fit.
+  const int n32 = (int)a.n;
+  const int rb0 = TAGGED ? a.box_of[(int)row0] : 0;
+  const int nrb = TAGGED ? a.box_of[min((int)row0 + MB, n32) - 1] - rb0 + 1 : 1;
+  const bool tau_smem = TAGGED && (int64_t)nrb * a.b <= Cfg<NBT>::kTauFloats;
+  if (tau_smem)
+    for (int idx = tid; idx < nrb * a.b; idx += kThreads)
+      S.taus[idx] = a.tau[(int64_t)rb0 * a.b + idx];
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = S.tmem_base;
-  // Boxes of this tile's rows (rows are box-major, so they form a range).
-  const int n32 = (int)a.n;
-  const int rb0 = TAGGED ? a.box_of[(int)row0] : 0;
-  const int nrb = TAGGED ? a.box_of[min((int)row0 + MB, n32) - 1] - rb0 + 1 : 1;
-  const bool staged_w = nrb <= kMaxRB;
   const float factor = entry_f32_factor<KERNEL>();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
+    // X tiles by TMA into the stages; each chunk's staged coordinates (and
+    // column boxes) by bulk copy into the point slots, kCS - 1 chunks ahead.
     if (lane == 0) {
-      int issued = 0;
+      const uint32_t pbytes = kQcBytes + (TAGGED ? KC * 4 : 0);
+      auto copy_points = [&](int cc) {
+        const int cs = cc % kCS;
+        tc::mbar_arrive_expect_tx(&S.cfull[cs], pbytes);
+        tc::bulk_load(S.qc[cs], a.qst + (int64_t)cc * (KC / 2 * 3), kQcBytes, &S.cfull[cs]);
+        if (TAGGED) tc::bulk_load(S.bq[cs], a.boxpad + (int64_t)cc * KC, KC * 4, &S.cfull[cs]);
+      };
+      int issued = 0, pissued = 0;
+      for (; pissued < kCS - 1 && pissued < nk; ++pissued) copy_points(pissued);
       for (int c = 0; c < nk && !S.abort; ++c) {
         const int s = c % STAGES;
         const uint32_t ph = (c / STAGES) & 1;
@@ -233,12 +249,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = 0; t < kParts; ++t)
           tc::tma_load_2d(S.x[s][t], &maps.part[t], &S.full_b[s], c * KC, col0);
         issued = c + 1;
+        if (pissued < nk) {
+          // Slot of chunk pissued is free once the generators released chunk pissued - kCS.
+          const int cs = pissued % kCS;
+          if (pissued >= kCS && !wait_or_abort(S, a.status, &S.cfree[cs], ((pissued / kCS) & 1) ^ 1))
+            break;
+          copy_points(pissued++);
+        }
       }
       // Copies still in flight must land before the CTA exits.
       for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c) {
         const uint32_t ph = (c / STAGES) & 1;
         const long long t0 = clock64();
         while (!tc::mbar_try_wait(&S.full_b[c % STAGES], ph) && clock64() - t0 < kWaitBudget) {
+        }
+      }
+      for (int c = (pissued > kCS ? pissued - kCS : 0); c < pissued; ++c) {
+        const uint32_t ph = (c / kCS) & 1;
+        const long long t0 = clock64();
+        while (!tc::mbar_try_wait(&S.cfull[c % kCS], ph) && clock64() - t0 < kWaitBudget) {
         }
       }
     }
@@ -361,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else if (warp < kStageWarp) {
+  } else {
     // ---------------------------------------------------------- generators
     // Thread (j, rbase): rows rbase + 32 i (i < 4) x points 8 j .. 8 j + 7 of
     // each chunk, two points at a time in packed FP32x2 arithmetic.
@@ -370,20 +399,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int rbase = gt >> 3;
     const int prow0 = (int)row0 + rbase;         // n < 2^30 is checked on the host
     float2 rx[4][3], lx[4][3];                   // row coordinates, hi and lo, as (v, v) pairs
-    int rbi[4], brow[4];
+    const float *trow[4];                        // tau(box of the row, :)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int p = prow0 + 32 * i;
       const int bx = (TAGGED && p < n32) ? a.box_of[p] : rb0;
-      rbi[i] = bx - rb0;
-      brow[i] = bx * a.b;
+      trow[i] = tau_smem ? S.taus + (bx - rb0) * a.b : a.tau + (int64_t)bx * a.b;
+      // Point p in the staged layout: chunk p / 64, pair P = (p % 64) / 2 = 4 j + pr.
+      const int w = p & (KC - 1), P = w >> 1, u = w & 1;
+      const float4 *blk = a.qst + (int64_t)(p / KC) * (KC / 2 * 3) + (P & 3) * 8 + (P >> 2);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 f0 = p < n32 ? blk[0] : z4, f1 = p < n32 ? blk[32] : z4;
+      const float4 f2 = p < n32 ? blk[64] : z4;
+      const float v[6] = {u ? f0.y : f0.x, u ? f0.w : f0.z, u ? f1.y : f1.x,
+                          u ? f1.w : f1.z, u ? f2.y : f2.x, u ? f2.w : f2.z};
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
-        const bool in = ax < a.d && p < n32;
-        const float h = in ? a.ch[ax * a.npad + p] : 0.f;
-        const float l = in ? a.cl[ax * a.npad + p] : 0.f;
-        rx[i][ax] = make_float2(h, h);
-        lx[i][ax] = make_float2(l, l);
+        rx[i][ax] = make_float2(-v[ax], -v[ax]);
+        lx[i][ax] = make_float2(-v[3 + ax], -v[3 + ax]);
       }
     }
     const float2 f2 = make_float2(factor, factor);
@@ -397,10 +430,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int kc0 = c * KC;
       const bool clean = (kc0 + KC <= (int)row0 || kc0 >= (int)row0 + MB) && kc0 + KC <= n32 &&
                          (int)row0 + MB <= n32;
+      // Tag weights: a chunk inside one column box has one weight per row.
+      int bq0 = 0;
+      bool one_box = true;
+      if (TAGGED) {
+        bq0 = S.bq[cs][0];
+        one_box = bq0 == S.bq[cs][KC - 1];
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int r = rbase + 32 * i, p = prow0 + 32 * i;
         uint32_t pw[kParts][4];
+        float wrow = factor;
+        if (TAGGED && one_box) wrow = factor * trow[i][bq0];
 #pragma unroll
         for (int pr = 0; pr < 4; ++pr) {
           const int P = 4 * j + pr;  // point pair within the chunk
@@ -420,11 +462,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float2 e = make_float2(entry_f32_of_r2<KERNEL>(r2.x), entry_f32_of_r2<KERNEL>(r2.y));
           float2 w = f2;
           if (TAGGED) {
-            if (staged_w)
-              w = S.wt[cs][rbi[i]][pr][j];
+            if (one_box)
+              w = make_float2(wrow, wrow);
             else
-              w = make_float2(factor * a.tau[brow[i] + S.bq[cs][2 * P]],
-                              factor * a.tau[brow[i] + S.bq[cs][2 * P + 1]]);
+              w = make_float2(factor * trow[i][S.bq[cs][2 * P]], factor * trow[i][S.bq[cs][2 * P + 1]]);
           }
           float2 v = __fmul2_rn(e, w);
           if (!clean) {
@@ -447,40 +488,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::mbar_arrive(&S.full_a[s]);
       }
     }
-  } else {
-    // -------------------------------------------------------------- stager
-    // Stages chunk c's point data into slot c % kCS as soon as the generators
-    // have released it (lane l takes points 2l, 2l + 1), so the generators
-    // never wait on global memory.
-    for (int c = 0; c < nk && !warp_aborted(S); ++c) {
-      const int cs = c % kCS;
-      if (c >= kCS && !warp_wait(S, a.status, &S.cfree[cs], ((c / kCS) & 1) ^ 1)) break;
-      const int64_t q = (int64_t)c * KC + 2 * lane;
-      float2 h[3], l[3];
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        h[ax] = ax < a.d ? *reinterpret_cast<const float2 *>(a.ch + ax * a.npad + q)
-                         : make_float2(0.f, 0.f);
-        l[ax] = ax < a.d ? *reinterpret_cast<const float2 *>(a.cl + ax * a.npad + q)
-                         : make_float2(0.f, 0.f);
-      }
-      const int pj = lane >> 2, pr = lane & 3;  // this lane's pair P = lane = 4 pj + pr
-      S.qc[cs][0][pr][pj] = make_float4(-h[0].x, -h[0].y, -h[1].x, -h[1].y);
-      S.qc[cs][1][pr][pj] = make_float4(-h[2].x, -h[2].y, -l[0].x, -l[0].y);
-      S.qc[cs][2][pr][pj] = make_float4(-l[1].x, -l[1].y, -l[2].x, -l[2].y);
-      if (TAGGED) {
-        const int b0 = a.box_of[min((int)q, n32 - 1)], b1 = a.box_of[min((int)q + 1, n32 - 1)];
-        S.bq[cs][2 * lane] = b0;
-        S.bq[cs][2 * lane + 1] = b1;
-        if (staged_w)
-          for (int rb = 0; rb < nrb; ++rb) {
-            const float *tr = a.tau + (int64_t)(rb0 + rb) * a.b;
-            S.wt[cs][rb][pr][pj] = make_float2(factor * tr[b0], factor * tr[b1]);
-          }
-      }
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&S.cfull[cs]);
-    }
   }
 
   tc::tc_fence_before();
@@ -491,21 +498,38 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Coordinates as hi/lo floats (x = hi + lo to ~48 bits), zero padded to npad.
-__global__ void split_coords_kernel(const double *__restrict__ pts, int64_t n, int64_t npad, int d,
-                                    float *__restrict__ ch, float *__restrict__ cl) {
-  const int64_t total = npad * d;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ax = i / npad, p = i % npad;
-    float h = 0.f, l = 0.f;
-    if (p < n) {
-      const double x = pts[ax * n + p];
-      h = (float)x;
-      l = (float)(x - (double)h);
+// Coordinates as negated double-float pairs (x = hi + lo to ~48 bits) in the
+// staged layout the tensor-core kernel copies per chunk: chunk c, point pair
+// P = 4 j + pr at qst[c][f][pr][j] with f = {xh, yh}, {zh, xl}, {yl, zl} for
+// the pair (points past n are zero), and the box of each point padded to npad
+// with the last box.
+__global__ void stage_coords_kernel(const double *__restrict__ pts, const int32_t *__restrict__ box_of,
+                                    int64_t n, int64_t npad, int d, float4 *__restrict__ qst,
+                                    int32_t *__restrict__ boxpad) {
+  const int64_t npairs = npad / 2;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npairs;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / (KC / 2);
+    const int P = (int)(t % (KC / 2)), j = P >> 2, pr = P & 3;
+    float h[2][3], l[2][3];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t p = 2 * t + u;
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        h[u][ax] = l[u][ax] = 0.f;
+        if (ax < d && p < n) {
+          const double x = pts[ax * n + p];
+          h[u][ax] = (float)x;
+          l[u][ax] = (float)(x - (double)h[u][ax]);
+        }
+      }
+      if (boxpad) boxpad[p] = box_of[p < n ? p : n - 1];
     }
-    ch[i] = h;
-    cl[i] = l;
+    float4 *blk = qst + c * (KC / 2 * 3) + pr * 8 + j;
+    blk[0] = make_float4(-h[0][0], -h[1][0], -h[0][1], -h[1][1]);
+    blk[32] = make_float4(-h[0][2], -h[1][2], -l[0][0], -l[1][0]);
+    blk[64] = make_float4(-l[0][1], -l[1][1], -l[0][2], -l[1][2]);
   }
 }
 
@@ -584,7 +608,7 @@ ColTiles col_tiles(int64_t ncols, bool tagged) {
 
 struct MixedLayout {
   int64_t npad, ncols_pad;
-  size_t head, coords, planes, tau, total;
+  size_t head, coords, planes, tau, boxes, total;
 };
 
 MixedLayout mixed_layout(const Prob &P, int64_t ncols, bool tagged) {
@@ -595,7 +619,8 @@ MixedLayout mixed_layout(const Prob &P, int64_t ncols, bool tagged) {
   L.coords = align256(sizeof(float) * 2 * 3 * L.npad);
   L.planes = align256(sizeof(__nv_bfloat16) * L.npad * L.ncols_pad);
   L.tau = tagged ? align256(sizeof(float) * P.b * P.b) : 0;
-  L.total = L.head + L.coords + kParts * L.planes + L.tau;
+  L.boxes = tagged ? align256(sizeof(int32_t) * L.npad) : 0;
+  L.total = L.head + L.coords + kParts * L.planes + L.tau + L.boxes;
   return L;
 }
 
@@ -663,10 +688,11 @@ int dispatch_mixed(int kernel, int width, const Maps &maps, const MixedArgs &a, 
   return TBLR_EUNSUPPORTED;
 }
 
-MixedArgs base_args(const Prob &P, const MixedLayout &L, float *ch, float *cl, volatile int *status) {
+MixedArgs base_args(const Prob &P, const MixedLayout &L, const float4 *qst, const int32_t *boxpad,
+                    volatile int *status) {
   MixedArgs a{};
-  a.ch = ch;
-  a.cl = cl;
+  a.qst = qst;
+  a.boxpad = boxpad;
   a.n = P.n;
   a.npad = L.npad;
   a.d = P.d;
@@ -711,20 +737,19 @@ int apply_mixed(const Prob &P, const tblr_layout *lay, const double *xt, int64_t
   TBLR_REQUIRE((reinterpret_cast<uintptr_t>(ws) & 255) == 0, "workspace must be 256-byte aligned");
   char *w = static_cast<char *>(ws);
   int *status = reinterpret_cast<int *>(w);
-  float *ch = reinterpret_cast<float *>(w + L.head);
-  float *cl = ch + 3 * L.npad;
+  float4 *qst = reinterpret_cast<float4 *>(w + L.head);
   const Planes pl = planes_of(w, L);
   TBLR_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-  split_coords_kernel<<<(unsigned)std::min<int64_t>(cdiv(3 * L.npad, 256), 4096), 256, 0, s>>>(
-      lay->pts, P.n, L.npad, P.d, ch, cl);
-  TBLR_TRY(launch_status("split_coords_kernel"));
+  stage_coords_kernel<<<(unsigned)std::min<int64_t>(cdiv(L.npad / 2, 256), 4096), 256, 0, s>>>(
+      lay->pts, lay->box_of, P.n, L.npad, P.d, qst, nullptr);
+  TBLR_TRY(launch_status("stage_coords_kernel"));
   split_x_kernel<<<(unsigned)std::min<int64_t>(cdiv(L.npad * L.ncols_pad, 256), 152 * 32), 256, 0,
                    s>>>(xt, P.n, ncols, L.npad, L.ncols_pad, pl.part[0], pl.part[1], pl.part[2]);
   TBLR_TRY(launch_status("split_x_kernel"));
   const ColTiles ct = col_tiles(ncols, false);
   Maps maps;
   TBLR_TRY(make_maps(&maps, pl, L, ct.width));
-  MixedArgs a = base_args(P, L, ch, cl, status);
+  MixedArgs a = base_args(P, L, qst, nullptr, status);
   a.ncols = ncols;
   a.ldy = ldy;
   a.y = y;
@@ -747,14 +772,14 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
   TBLR_REQUIRE((reinterpret_cast<uintptr_t>(ws) & 255) == 0, "workspace must be 256-byte aligned");
   char *w = static_cast<char *>(ws);
   int *status = reinterpret_cast<int *>(w);
-  float *ch = reinterpret_cast<float *>(w + L.head);
-  float *cl = ch + 3 * L.npad;
+  float4 *qst = reinterpret_cast<float4 *>(w + L.head);
   const Planes pl = planes_of(w, L);
   float *tf = reinterpret_cast<float *>(w + L.head + L.coords + kParts * L.planes);
+  int32_t *boxpad = reinterpret_cast<int32_t *>(w + L.head + L.coords + kParts * L.planes + L.tau);
   TBLR_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-  split_coords_kernel<<<(unsigned)std::min<int64_t>(cdiv(3 * L.npad, 256), 4096), 256, 0, s>>>(
-      lay->pts, P.n, L.npad, P.d, ch, cl);
-  TBLR_TRY(launch_status("split_coords_kernel"));
+  stage_coords_kernel<<<(unsigned)std::min<int64_t>(cdiv(L.npad / 2, 256), 4096), 256, 0, s>>>(
+      lay->pts, lay->box_of, P.n, L.npad, P.d, qst, boxpad);
+  TBLR_TRY(launch_status("stage_coords_kernel"));
   split_gh_kernel<<<(unsigned)std::min<int64_t>(cdiv(L.npad * L.ncols_pad, 256), 152 * 32), 256, 0,
                     s>>>(G, H, lay->perm, P.n, P.r, L.npad, L.ncols_pad, pl.part[0], pl.part[1],
                          pl.part[2]);
@@ -765,7 +790,7 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
   const ColTiles ct = col_tiles(ncols, true);
   Maps maps;
   TBLR_TRY(make_maps(&maps, pl, L, ct.width));
-  MixedArgs a = base_args(P, L, ch, cl, status);
+  MixedArgs a = base_args(P, L, qst, boxpad, status);
   a.ncols = ncols;
   a.ldy = P.r;
   a.y = S;

@@ -26,43 +26,51 @@ __device__ __forceinline__ void load_point(const double *__restrict__ pts, int64
   }
 }
 
-// CTA per (i, j): a register-tiled FP32 GEMM.  Rows of box i go in chunks of
-// RC; for each chunk W = A(chunk, I_j) V_j is accumulated over 32-point steps
-// (the generated 32 x RC kernel tile and the 32 x KP slice of V_j in shared
-// memory, 4 x 4 outputs per thread, Kahan flush per step), then
-// Atilde_ij += U_i(chunk)^T W with U's rows staged in shared memory.
+// CTA per (i, j): a register-tiled FP32 GEMM on the packed FP32x2 pipes.
+// Rows of box i go in chunks of RC; for each chunk W = A(chunk, I_j) V_j is
+// accumulated over KT-point steps: the CTA generates the KT x RC kernel tile
+// into shared memory (two rows at a time in FP32x2 arithmetic from double-float
+// coordinates) next to the step's rows of V_j stored as duplicated pairs
+// (v, v), and each thread updates an 8 x 4 block of W as 4 x 4 row pairs with
+// one FFMA2 per pair (a 16-FFMA2 inner step from four 16-byte loads).  Each
+// step's FP32 sum (64 terms) is added to a running FP32 sum, so a W entry
+// carries ~sqrt(64) + sqrt(m_j / 64) roundings instead of sqrt(m_j).  Then
+// Atilde_ij += U_i(chunk)^T W with U's rows and W in shared memory (aliasing
+// the step buffers).
 template <int KP>
 struct CouplingShape {
-  static constexpr int TX = KP / 4;       // threads across W's columns
-  static constexpr int TY = 256 / TX;     // threads across W's rows
-  static constexpr int RC = 4 * TY;       // rows per chunk
+  static constexpr int TX = KP / 4;       // threads across W's columns (4 each)
+  static constexpr int TY = 256 / TX;     // threads across W's rows (8 each)
+  static constexpr int RC = 8 * TY;       // rows per chunk
   static constexpr int AT = KP / 16;      // Atilde tile edge per thread (16 x 16 threads)
-  static constexpr int KT = 32;           // points per K step
+  static constexpr int KT = 64;           // points per K step
+  static constexpr int AS = RC + 4;       // row stride of the generated tile
+  static constexpr size_t kStep = sizeof(float) * KT * AS + sizeof(float2) * KT * KP;
+  static constexpr size_t kChunk = sizeof(float) * 2 * (size_t)RC * (KP + 4);
+  static constexpr size_t kBuf = kStep > kChunk ? kStep : kChunk;
+  static constexpr size_t kBytes = kBuf + sizeof(float4) * 3 * (RC / 2) + sizeof(float) * 6 * KT;
 };
 
 template <int KP>
 size_t coupling_f32_smem_bytes() {
-  using C = CouplingShape<KP>;
-  return sizeof(float) * ((size_t)C::KT * (C::RC + 4) + (size_t)C::KT * KP + 6 * (size_t)C::RC +
-                          6 * (size_t)C::KT + 2 * (size_t)C::RC * (KP + 4));
+  return CouplingShape<KP>::kBytes;
 }
 
 template <int KERNEL, int KP>
-__global__ void __launch_bounds__(kThreads) coupling_f32_kernel(
+__global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
     const double *__restrict__ pts, int64_t n, int d, const int32_t *__restrict__ offsets,
     const int32_t *__restrict__ ranks, const double *__restrict__ U, const double *__restrict__ V,
     int k, int b, double *__restrict__ At) {
   using C = CouplingShape<KP>;
-  constexpr int TX = C::TX, RC = C::RC, AT = C::AT, KT = C::KT;
-  extern __shared__ float sf[];
-  float *Ak = sf;                          // [KT][RC + 4]  generated A(chunk rows, step points)
-  float *Vk = Ak + KT * (RC + 4);          // [KT][KP]      V_j rows of the step
-  float *rch = Vk + KT * KP;               // [3][RC] row coordinates, hi
-  float *rcl = rch + 3 * RC;               // [3][RC] lo
-  float *qch = rcl + 3 * RC;               // [3][KT] column coordinates, hi
-  float *qcl = qch + 3 * KT;               // [3][KT] lo
-  float *Ws = qcl + 3 * KT;                // [RC][KP + 4]
-  float *Us = Ws + RC * (KP + 4);          // [RC][KP + 4]
+  constexpr int TX = C::TX, RC = C::RC, AT = C::AT, KT = C::KT, AS = C::AS;
+  extern __shared__ __align__(16) float sf[];
+  float *Ak = sf;                                            // [KT][AS]  A(step point, chunk row)
+  float2 *Vd = reinterpret_cast<float2 *>(sf + KT * AS);     // [KT][KP]  (v, v) pairs of V_j
+  float *Ws = sf;                                            // [RC][KP + 4]  (aliases Ak, Vd)
+  float *Us = sf + RC * (KP + 4);                            // [RC][KP + 4]
+  float4 *rc = reinterpret_cast<float4 *>(reinterpret_cast<char *>(sf) + C::kBuf);
+  // rc[3 * pr + f]: row pair pr's coordinates {xh, yh}, {zh, xl}, {yl, zl}
+  float *qs = reinterpret_cast<float *>(rc + 3 * (RC / 2));  // [6][KT] step point coordinates
   const int i = blockIdx.x, j = blockIdx.y, tid = threadIdx.x;
   const int oi = offsets[i], mi = offsets[i + 1] - oi;
   const int oj = offsets[j], mj = offsets[j + 1] - oj;
@@ -72,8 +80,10 @@ __global__ void __launch_bounds__(kThreads) coupling_f32_kernel(
     for (int idx = tid; idx < k * k; idx += kThreads) out[idx] = 0.0;
     return;
   }
-  const int tx = tid % TX, ty = tid / TX;       // W tile: rows 4ty.., columns 4tx..
+  const int tx = tid % TX, ty = tid / TX;       // W block: rows 8 ty .., columns 4 tx ..
   const int ta = tid / 16, tc = tid % 16;       // Atilde tile: rows AT*ta.., columns AT*tc..
+  const int lane = tid & 31, warp = tid >> 5;  // generation: points warp + 8 v, row pairs lane + 32 u
+  const float factor = entry_f32_factor<KERNEL>();
   float thi[AT][AT], tcc[AT][AT];
 #pragma unroll
   for (int x = 0; x < AT; ++x)
@@ -82,70 +92,115 @@ __global__ void __launch_bounds__(kThreads) coupling_f32_kernel(
 
   for (int r0 = 0; r0 < mi; r0 += RC) {
     __syncthreads();
-    for (int idx = tid; idx < 3 * RC; idx += kThreads) {
-      const int ax = idx / RC, r = idx % RC;
-      float h = 0.f, l = 0.f;
-      if (ax < d && r0 + r < mi) split_coord(pts[ax * n + oi + r0 + r], h, l);
-      rch[idx] = h;
-      rcl[idx] = l;
+    for (int pr = tid; pr < RC / 2; pr += kThreads) {
+      float h[2][3], l[2][3];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int r = r0 + 2 * pr + u;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          h[u][ax] = l[u][ax] = 0.f;
+          if (ax < d && r < mi) split_coord(pts[ax * n + oi + r], h[u][ax], l[u][ax]);
+        }
+      }
+      rc[3 * pr + 0] = make_float4(h[0][0], h[1][0], h[0][1], h[1][1]);
+      rc[3 * pr + 1] = make_float4(h[0][2], h[1][2], l[0][0], l[1][0]);
+      rc[3 * pr + 2] = make_float4(l[0][1], l[1][1], l[0][2], l[1][2]);
     }
-    float acc[4][4], hi[4][4], cc[4][4];
+    float2 acc[4][4], hi[4][4];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) acc[x][y] = hi[x][y] = cc[x][y] = 0.f;
+      for (int y = 0; y < 4; ++y) acc[x][y] = hi[x][y] = make_float2(0.f, 0.f);
     for (int q0 = 0; q0 < mj; q0 += KT) {
       __syncthreads();
-      for (int idx = tid; idx < 3 * KT; idx += kThreads) {
-        const int ax = idx / KT, q = idx % KT;
-        float h = 0.f, l = 0.f;
-        if (ax < d && q0 + q < mj) split_coord(pts[ax * n + oj + q0 + q], h, l);
-        qch[idx] = h;
-        qcl[idx] = l;
-      }
+      // Step rows of V_j as (v, v) pairs, interleaved so that the column pairs
+      // (4 tx, 4 tx + 1) of all tx come first, then (4 tx + 2, 4 tx + 3): each of
+      // a thread's two 16-byte loads then reads a contiguous run across tx.
       for (int idx = tid; idx < KT * KP; idx += kThreads) {
         const int q = idx / KP, c = idx % KP;
-        Vk[idx] = (q0 + q < mj && c < kj) ? (float)V[((int64_t)oj + q0 + q) * k + c] : 0.f;
+        const float v = (q0 + q < mj && c < kj) ? (float)V[((int64_t)oj + q0 + q) * k + c] : 0.f;
+        const int ctx = c >> 2, half = (c >> 1) & 1, e = c & 1;
+        Vd[((q * 2 + half) * TX + ctx) * 2 + e] = make_float2(v, v);
       }
-      __syncthreads();
-      {
-        const int q = tid % KT;
-        const float qh[3] = {qch[q], qch[KT + q], qch[2 * KT + q]};
-        const float ql[3] = {qcl[q], qcl[KT + q], qcl[2 * KT + q]};
-        const bool qin = q0 + q < mj;
-        for (int r = tid / KT; r < RC; r += kThreads / KT) {
-          const float rh[3] = {rch[r], rch[RC + r], rch[2 * RC + r]};
-          const float rl[3] = {rcl[r], rcl[RC + r], rcl[2 * RC + r]};
-          float v = entry_f32<KERNEL>(rh, rl, qh, ql);
-          if (!qin || r0 + r >= mi || (i == j && r0 + r == q0 + q)) v = 0.f;
-          Ak[q * (RC + 4) + r] = v;
+      // The step's point coordinates (negated double-float pairs).
+      for (int q = tid; q < KT; q += kThreads) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          float h = 0.f, l = 0.f;
+          if (ax < d && q0 + q < mj) split_coord(pts[ax * n + oj + q0 + q], h, l);
+          qs[ax * KT + q] = -h;
+          qs[(3 + ax) * KT + q] = -l;
         }
       }
       __syncthreads();
-#pragma unroll 8
+      // Kernel tile: each warp takes points warp + 8 v (coordinates warp-uniform,
+      // negated and broadcast as pairs), its lanes consecutive row pairs, so the
+      // 8-byte stores of a warp are contiguous.
+      const float2 f2 = make_float2(factor, factor);
+      for (int gq = warp; gq < KT; gq += kThreads / 32) {
+        const bool qin = q0 + gq < mj;
+        const float2 nxh = make_float2(qs[gq], qs[gq]), nyh = make_float2(qs[KT + gq], qs[KT + gq]);
+        const float2 nzh = make_float2(qs[2 * KT + gq], qs[2 * KT + gq]);
+        const float2 nxl = make_float2(qs[3 * KT + gq], qs[3 * KT + gq]);
+        const float2 nyl = make_float2(qs[4 * KT + gq], qs[4 * KT + gq]);
+        const float2 nzl = make_float2(qs[5 * KT + gq], qs[5 * KT + gq]);
+        for (int pr = lane; pr < RC / 2; pr += 32) {
+          const float4 c0 = rc[3 * pr], c1 = rc[3 * pr + 1], c2 = rc[3 * pr + 2];
+          const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(c0.x, c0.y), nxh),
+                                       __fadd2_rn(make_float2(c1.z, c1.w), nxl));
+          const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(c0.z, c0.w), nyh),
+                                       __fadd2_rn(make_float2(c2.x, c2.y), nyl));
+          float2 r2;
+          if (KERNEL == TBLR_KERNEL_LAPLACE3D) {
+            const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(c1.x, c1.y), nzh),
+                                         __fadd2_rn(make_float2(c2.z, c2.w), nzl));
+            r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+          } else {
+            r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+          }
+          float2 v = __fmul2_rn(make_float2(entry_f32_of_r2<KERNEL>(r2.x),
+                                            entry_f32_of_r2<KERNEL>(r2.y)), f2);
+          const int rr = r0 + 2 * pr;
+          if (!qin || rr >= mi || (i == j && rr == q0 + gq)) v.x = 0.f;
+          if (!qin || rr + 1 >= mi || (i == j && rr + 1 == q0 + gq)) v.y = 0.f;
+          *reinterpret_cast<float2 *>(Ak + gq * AS + 2 * pr) = v;
+        }
+      }
+      __syncthreads();
+#pragma unroll 4
       for (int q = 0; q < KT; ++q) {
-        const float4 av = *reinterpret_cast<const float4 *>(Ak + q * (RC + 4) + 4 * ty);
-        const float4 vv = *reinterpret_cast<const float4 *>(Vk + q * KP + 4 * tx);
-        const float a4[4] = {av.x, av.y, av.z, av.w};
-        const float v4[4] = {vv.x, vv.y, vv.z, vv.w};
+        const float4 a0 = *reinterpret_cast<const float4 *>(Ak + q * AS + 8 * ty);
+        const float4 a1 = *reinterpret_cast<const float4 *>(Ak + q * AS + 8 * ty + 4);
+        const float4 v0 = *reinterpret_cast<const float4 *>(Vd + ((q * 2 + 0) * TX + tx) * 2);
+        const float4 v1 = *reinterpret_cast<const float4 *>(Vd + ((q * 2 + 1) * TX + tx) * 2);
+        const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
+                              make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
+        const float2 vp[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w),
+                              make_float2(v1.x, v1.y), make_float2(v1.z, v1.w)};
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a4[x], v4[y], acc[x][y]);
+          for (int y = 0; y < 4; ++y) acc[x][y] = __ffma2_rn(ap[x], vp[y], acc[x][y]);
       }
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
-          kahan_add(hi[x][y], cc[x][y], acc[x][y]);
-          acc[x][y] = 0.f;
+          hi[x][y] = __fadd2_rn(hi[x][y], acc[x][y]);
+          acc[x][y] = make_float2(0.f, 0.f);
         }
     }
-    // W chunk and U rows to shared memory, then Atilde += U^T W.
+    // W chunk and U rows to shared memory (over the step buffers), then
+    // Atilde += U^T W.
+    __syncthreads();
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) Ws[(4 * ty + x) * (KP + 4) + 4 * tx + y] = hi[x][y] - cc[x][y];
+      for (int y = 0; y < 4; ++y) {
+        Ws[(8 * ty + 2 * x) * (KP + 4) + 4 * tx + y] = hi[x][y].x;
+        Ws[(8 * ty + 2 * x + 1) * (KP + 4) + 4 * tx + y] = hi[x][y].y;
+      }
     for (int idx = tid; idx < RC * KP; idx += kThreads) {
       const int r = idx / KP, a = idx % KP;
       Us[r * (KP + 4) + a] =
