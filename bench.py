@@ -47,7 +47,7 @@ WORKLOADS = {
     # 3D Laplace, jittered 64^3 lattice (jitter U[-h/4, h/4]), 8 x 8 x 8 boxes of 512 points,
     # k = 64; run with --precision mixed
     "laplace3d_n262144": dict(d=3, n=262144, grid=(8, 8, 8), k=64, p=10, e=3, kernel="laplace3d",
-                              seed=0x7A660003, lattice=64, cpu_boxes=1),
+                              seed=0x7A660003, lattice=64, cpu_boxes=2),
     # same recipe on a 32^3 lattice, 4 x 4 x 4 boxes of 512 points
     "laplace3d_n32768": dict(d=3, n=32768, grid=(4, 4, 4), k=64, p=10, e=3, kernel="laplace3d",
                              seed=0x7A660013, lattice=32, cpu_boxes=2),
