@@ -84,6 +84,8 @@ def make_inputs(w, rank=0):
     b = int(np.prod(w["grid"]))
     ell = 3 ** d + 1 + w["e"]
     T, G, H = inputs.tagging_draws(b, ell, w["n"], w["k"] + w["p"], seed=w["seed"] + 1 + 7919 * rank)
+    if w.get("selfadjoint"):
+        H = G  # Psi = Omega: the self-adjoint mode's R = S
     return pts, T, G, H
 
 
@@ -208,9 +210,10 @@ class Runner:
         self.pts, self.T, self.G, self.H = t(pts), t(T), t(G), t(H)
         d = w["d"]
         self.tagged = w.get("sketch", 0) == 1
+        self.selfadjoint = bool(w.get("selfadjoint"))
         self.prob = tb.make_problem(d, w["kernel"], w["n"], w["grid"], (0.0,) * d, (1.0,) * d,
                                     w["k"], w["p"], w["e"], precision=w.get("precision", 0),
-                                    sketch=w.get("sketch", 0))
+                                    sketch=w.get("sketch", 0), selfadjoint=self.selfadjoint)
         self.sz = tb.tblr_sizes_of(self.prob)
         lay = tb.tblr_tessellate(self.prob, self.pts)
         nf_off, m_max = tb.tblr_nearfield_offsets(self.prob, lay)
@@ -244,7 +247,7 @@ class Runner:
         mixed = w.get("precision", 0) == 1
         base = 4 + 2 + 2 + 1 + 2 + 1 + (1 if mixed else 0)
         self.launches_per_step = base + ((4 if mixed else 2) if self.tagged else
-                                         (5 if mixed else 3))
+                                         (5 if mixed else 3)) - (1 if self.selfadjoint else 0)
 
     def step(self, ev=None):
         tb, L, P, o = self.tb, self.tb.lib(), self.tb.ctypes.byref(self.prob), self.out
@@ -280,8 +283,11 @@ class Runner:
             ck(L.tblr_combine(P, lay.ref, p(o.yz), p(o.z), p(self.S), p(self.R), s), "combine")
         ck(L.tblr_col(P, lay.ref, p(self.S), p(o.u), p(o.ranks), p(self.colws), self.colws.numel(),
                       s), "col U")
-        ck(L.tblr_col(P, lay.ref, p(self.R), p(o.v), p(o.ranks), p(self.colws), self.colws.numel(),
-                      s), "col V")
+        if self.selfadjoint:
+            o.v.copy_(o.u)  # R = S, so V = U (a device copy, no kernel)
+        else:
+            ck(L.tblr_col(P, lay.ref, p(self.R), p(o.v), p(o.ranks), p(self.colws),
+                          self.colws.numel(), s), "col V")
         ck(L.tblr_coupling(P, lay.ref, None, p(o.u), p(o.v), p(o.ranks), m_max, p(o.at), s),
            "coupling")
         ck(L.tblr_nearfield(P, lay.ref, None, p(o.u), p(o.at), p(o.v), p(o.ranks), p(o.nf_off),
@@ -334,7 +340,8 @@ def mixed_vs_fp64(tb, torch, w, run):
     from paper_2501_05528_gb300 import metrics
     d = w["d"]
     prob64 = tb.make_problem(d, w["kernel"], w["n"], w["grid"], (0.0,) * d, (1.0,) * d, w["k"],
-                             w["p"], w["e"], precision=tb.FP64, sketch=tb.SKETCH_TAGGED)
+                             w["p"], w["e"], precision=tb.FP64, sketch=tb.SKETCH_TAGGED,
+                             selfadjoint=bool(w.get("selfadjoint")))
     ref = tb.compress(prob64, run.pts, run.T, run.G, run.H)
     torch.cuda.synchronize()
     h = lambda t: t.cpu().numpy()
@@ -429,7 +436,7 @@ def run_gpu(args, w):
 
     result = None
     if rank == 0:
-        cols = 2 * sz.r if run.tagged else sz.sketch_cols
+        cols = (1 if run.selfadjoint else 2) * sz.r if run.tagged else sz.sketch_cols
         flops = 2.0 * w["n"] * w["n"] * cols
         sk = statistics.mean(sketch_ms) / 1e3
         achieved = flops / sk / 1e12
@@ -458,7 +465,8 @@ def run_gpu(args, w):
                        "grid": list(w["grid"]), "k": w["k"], "p": w["p"], "e": w["e"],
                        "ell": sz.ell, "sketch_cols": sz.sketch_cols, "kernel": w["kernel"],
                        "precision": "fp64" if w.get("precision", 0) == 0 else "mixed",
-                       "sketch": "tagged" if run.tagged else "blackbox",
+                       "sketch": ("tagged, self-adjoint (H = G, V = U)" if run.selfadjoint else
+                                  "tagged") if run.tagged else "blackbox",
                        "l2": "flushed by a 256 MiB write before every step",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
@@ -658,6 +666,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the mixed-vs-FP64 accuracy check of the mixed path")
+    ap.add_argument("--selfadjoint", action="store_true",
+                    help="self-adjoint mode (A = A^T, H = G): V = U, half the coupling")
     ap.add_argument("--sketch", default="blackbox", choices=["blackbox", "tagged"],
                     help="black-box sketch Y = A Omega (the paper's order) or the tag-factored S, R")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
@@ -673,6 +683,10 @@ def main():
     w = dict(WORKLOADS[args.workload])
     w["precision"] = 1 if args.precision == "mixed" else 0
     w["sketch"] = 1 if args.sketch == "tagged" else 0
+    if args.selfadjoint:
+        if w["sketch"] != 1:
+            raise SystemExit("--selfadjoint needs --sketch tagged")
+        w["selfadjoint"] = True
     if args.impl == "reference":
         res = run_reference(args, w)
     elif args.mode == "batch":

@@ -57,7 +57,7 @@ extern "C" {
 
 /* Precision mode (see "Floating point" above). */
 #define TBLR_FP64  0
-#define TBLR_MIXED 1  /* split-FP16 tensor-core sketch; FP32 coupling and near field */
+#define TBLR_MIXED 1  /* three-part BF16 tensor-core sketch; FP32 coupling and near field */
 
 /* Near-field reading (§6.1): the paper's identity probe, or the exact block. */
 #define TBLR_NEARFIELD_PROBE 0  /* B_ij = sum_{c: colour(c)=colour(j)} (A_ic - U_i At_ic V_c^T)(:, 0:m_j) */
@@ -73,6 +73,13 @@ extern "C" {
  *   terms weighted by tau_i(c) ~ 0 instead of cancelling between sketches. */
 #define TBLR_SKETCH_BLACKBOX 0
 #define TBLR_SKETCH_TAGGED   1
+/* Flag, or-ed into TBLR_SKETCH_TAGGED: the caller guarantees A = A^T and
+ * passes H = G (Psi = Omega).  Then R = S and V = U (the adjoint sketch of
+ * the paper coincides with the direct one when A is self-adjoint), so only S
+ * is formed, col runs once and V is a copy of U, and the coupling is formed
+ * for i <= j with Atilde_ji = Atilde_ij^T (Atilde_ij = U_i^T A_ij U_j).  The
+ * near field is unchanged.  Needs the tag-factored sketch. */
+#define TBLR_SKETCH_SELFADJOINT 2
 
 /* Problem statement: geometry and tessellation, admissibility, rank
  * (Algorithm 2 "Require": a b x b tessellation of a d-dimensional geometry,
@@ -89,7 +96,7 @@ typedef struct {
     int32_t e;          /* extra tag columns, >= 0 (the paper uses 3) */
     int32_t precision;  /* TBLR_FP64 or TBLR_MIXED */
     int32_t nearfield;  /* TBLR_NEARFIELD_PROBE or TBLR_NEARFIELD_EXACT */
-    int32_t sketch;     /* TBLR_SKETCH_BLACKBOX or TBLR_SKETCH_TAGGED (tblr_compress) */
+    int32_t sketch;     /* TBLR_SKETCH_BLACKBOX or TBLR_SKETCH_TAGGED, optionally | TBLR_SKETCH_SELFADJOINT */
 } tblr_problem;
 
 /* Sizes that follow from a problem (no device work). */
@@ -196,8 +203,9 @@ int tblr_sketch(const tblr_problem *prob, const tblr_layout *lay, const double *
  * A_ic G_c and R(I_i, :) = sum_c tau[i, c] (A^T)_ic H_c directly from the
  * projected tags tau (b x b, from tblr_decode) and G, H ([n*r], original point
  * order).  s, rr: [n*r] box-major.  FP64, or with TBLR_MIXED on the tensor
- * cores (split FP16, FP32 accumulation, FP32 tags).  The sketch Y, Z is never
- * formed.  ws: tblr_tagged_sketch_workspace bytes. */
+ * cores (three-part BF16, FP32 accumulation, FP32 tags).  The sketch Y, Z is
+ * never formed.  With TBLR_SKETCH_SELFADJOINT only s is written (H and rr may
+ * be NULL; R = S).  ws: tblr_tagged_sketch_workspace bytes. */
 size_t tblr_tagged_sketch_workspace(const tblr_problem *prob);
 int tblr_tagged_sketch(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
                        const double *tau, const double *G, const double *H, double *s,
@@ -222,7 +230,9 @@ int tblr_combine(const tblr_problem *prob, const tblr_layout *lay, const double 
  * U(I_i, 0:k_i) = k_i dominant left singular vectors of S(I_i, :), each column
  * signed so its largest-magnitude entry is positive (lowest index on ties);
  * columns k_i..k-1 are zero.  k_i = min(k, m_i), or 0 when F_i is empty.
- * Method: FP64 Householder QR, one-sided Jacobi SVD of R, Q applied back.
+ * Method: FP64 Householder QR; one-sided Jacobi SVD of R in FP32, its
+ * rotations re-orthonormalised in FP64 and polished by FP64 sweeps; Q applied
+ * back in FP64.
  * s: [n*r]; u: [n*k]; ranks: [b] (written).  ws: tblr_col_workspace bytes.
  * Limits: r <= 112. */
 size_t tblr_col_workspace(const tblr_problem *prob);
@@ -233,7 +243,9 @@ int tblr_col(const tblr_problem *prob, const tblr_layout *lay, const double *s,
  * Atilde_ij = U_i^T A_ij V_j for ALL box pairs: at[((i*b + j)*k + a)*k + c],
  * zero outside a < k_i, c < k_j.  u, v: [n*k]; ranks: [b]; m_max = max_i m_i
  * (as returned by tblr_nearfield_offsets).  FP64, or with TBLR_MIXED on the
- * FP32 pipes (double-float coordinates, compensated sums, ~1e-7 relative).
+ * FP32 pipes (double-float coordinates, chunked and compensated sums, ~1e-7
+ * relative).  With TBLR_SKETCH_SELFADJOINT the caller passes v = u (A = A^T)
+ * and only i <= j are formed, Atilde_ji = Atilde_ij^T.
  * Limits: k <= 64; mixed: m_max <= ~780. */
 int tblr_coupling(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
                   const double *u, const double *v, const int32_t *ranks, int32_t m_max,

@@ -15,10 +15,10 @@ struct WsPlan {
 
 WsPlan plan_workspace(const Prob &P, const tblr_problem *prob, int32_t m_max) {
   WsPlan w;
-  const bool tagged = prob->sketch == TBLR_SKETCH_TAGGED;
+  const bool tagged = P.tagged;
   w.omega = tagged ? 0 : align256(sizeof(double) * 2 * P.C * P.n);
   w.s = align256(sizeof(double) * P.n * P.r);
-  w.r = w.s;
+  w.r = P.selfadjoint ? 0 : w.s;
   w.col = align256(tblr_col_workspace(prob));
   w.sketch = align256(tagged ? tblr_tagged_sketch_workspace(prob) : tblr_sketch_workspace(prob));
   w.nf = align256(tblr_nearfield_workspace(prob, m_max));
@@ -42,7 +42,7 @@ extern "C" int tblr_compress(const tblr_problem *prob, const tblr_layout *lay, c
   Prob P;
   TBLR_TRY(check_problem(prob, &P));
   TBLR_TRY(check_layout(P, lay));
-  const bool tagged = prob->sketch == TBLR_SKETCH_TAGGED;
+  const bool tagged = P.tagged;
   TBLR_REQUIRE(T && G && H && (yz || tagged) && z && tau && rho && u && v && ranks && at &&
                    nf_off && bnear,
                "every input and output pointer must be non-NULL");
@@ -68,7 +68,13 @@ extern "C" int tblr_compress(const tblr_problem *prob, const tblr_layout *lay, c
     TBLR_TRY(tblr_combine(prob, lay, yz, z, S, R, stream));
   }
   TBLR_TRY(tblr_col(prob, lay, S, u, ranks, colws, w.col, stream));
-  TBLR_TRY(tblr_col(prob, lay, R, v, ranks, colws, w.col, stream));
+  if (P.selfadjoint) {
+    // A = A^T and H = G give R = S, hence V = U.
+    TBLR_CUDA(cudaMemcpyAsync(v, u, sizeof(double) * P.n * P.k, cudaMemcpyDeviceToDevice,
+                              as_stream(stream)));
+  } else {
+    TBLR_TRY(tblr_col(prob, lay, R, v, ranks, colws, w.col, stream));
+  }
   // Step II (Table 1): Atilde = U^T (A V).
   TBLR_TRY(tblr_coupling(prob, lay, dense, u, v, ranks, m_max, at, stream));
   // Step III (Table 1): near field from the identity probes.

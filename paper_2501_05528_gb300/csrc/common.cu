@@ -37,8 +37,10 @@ int check_problem(const tblr_problem *in, Prob *P) {
   TBLR_REQUIRE(in->precision == TBLR_FP64 || in->precision == TBLR_MIXED, "bad precision");
   TBLR_REQUIRE(in->nearfield == TBLR_NEARFIELD_PROBE || in->nearfield == TBLR_NEARFIELD_EXACT,
                "bad nearfield mode");
-  TBLR_REQUIRE(in->sketch == TBLR_SKETCH_BLACKBOX || in->sketch == TBLR_SKETCH_TAGGED,
-               "bad sketch mode");
+  TBLR_REQUIRE(in->sketch == TBLR_SKETCH_BLACKBOX || in->sketch == TBLR_SKETCH_TAGGED ||
+                   in->sketch == (TBLR_SKETCH_TAGGED | TBLR_SKETCH_SELFADJOINT),
+               "bad sketch mode %d (the self-adjoint flag needs the tag-factored sketch)",
+               in->sketch);
   P->d = in->d;
   P->kernel = in->kernel;
   P->n = in->n;
@@ -48,6 +50,8 @@ int check_problem(const tblr_problem *in, Prob *P) {
   P->r = in->k + in->p;
   P->precision = in->precision;
   P->nearfield = in->nearfield;
+  P->tagged = (in->sketch & TBLR_SKETCH_TAGGED) != 0;
+  P->selfadjoint = (in->sketch & TBLR_SKETCH_SELFADJOINT) != 0;
   int s3 = 1;
   for (int a = 0; a < in->d; ++a) s3 *= 3;
   P->s3 = s3;

@@ -634,18 +634,19 @@ int env_flush() {
   return f;
 }
 
-// [G | H] gathered to box-major order and split into BF16 h/m/l planes
-// [ncols_pad][npad] (rows c < r from G, r <= c < 2r from H, zero padded).
+// [G | H] (or G alone: ncols = r) gathered to box-major order and split into
+// BF16 h/m/l planes [ncols_pad][npad] (rows c < r from G, r <= c < ncols from
+// H, zero padded).
 __global__ void split_gh_kernel(const double *__restrict__ G, const double *__restrict__ H,
-                                const int32_t *__restrict__ perm, int64_t n, int r, int64_t npad,
-                                int64_t ncols_pad, __nv_bfloat16 *__restrict__ xh,
+                                const int32_t *__restrict__ perm, int64_t n, int r, int64_t ncols,
+                                int64_t npad, int64_t ncols_pad, __nv_bfloat16 *__restrict__ xh,
                                 __nv_bfloat16 *__restrict__ xm, __nv_bfloat16 *__restrict__ xl) {
   const int64_t total = npad * ncols_pad;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = i / npad, p = i % npad;
     double v = 0.0;
-    if (p < n && c < 2 * r) {
+    if (p < n && c < ncols) {
       const int64_t src = (int64_t)perm[p] * r + (c < r ? c : c - r);
       v = c < r ? G[src] : H[src];
     }
@@ -724,7 +725,9 @@ int make_maps(Maps *maps, const Planes &pl, const MixedLayout &L, int width) {
 }  // namespace
 
 size_t mixed_workspace(const Prob &P, int64_t ncols) { return mixed_layout(P, ncols, false).total; }
-size_t tagged_mixed_workspace(const Prob &P) { return mixed_layout(P, 2 * P.r, true).total; }
+size_t tagged_mixed_workspace(const Prob &P) {
+  return mixed_layout(P, (P.selfadjoint ? 1 : 2) * P.r, true).total;
+}
 
 int apply_mixed(const Prob &P, const tblr_layout *lay, const double *xt, int64_t ncols, double *y,
                 int64_t ldy, void *ws, size_t ws_bytes, cudaStream_t s) {
@@ -766,7 +769,8 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
                "mixed precision supports the built-in Laplace kernels");
   TBLR_REQUIRE(P.n < (int64_t)1 << 30, "mixed precision supports n < 2^30 points");
   TBLR_REQUIRE(P.b * P.b < (int64_t)1 << 31, "too many boxes for the tag table");
-  const int64_t ncols = 2 * P.r;
+  // Self-adjoint (H = G): only S = A' G, r columns.
+  const int64_t ncols = (P.selfadjoint ? 1 : 2) * P.r;
   const MixedLayout L = mixed_layout(P, ncols, true);
   TBLR_REQUIRE(ws != nullptr && ws_bytes >= L.total, "tagged sketch workspace too small");
   TBLR_REQUIRE((reinterpret_cast<uintptr_t>(ws) & 255) == 0, "workspace must be 256-byte aligned");
@@ -781,8 +785,8 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
       lay->pts, lay->box_of, P.n, L.npad, P.d, qst, boxpad);
   TBLR_TRY(launch_status("stage_coords_kernel"));
   split_gh_kernel<<<(unsigned)std::min<int64_t>(cdiv(L.npad * L.ncols_pad, 256), 152 * 32), 256, 0,
-                    s>>>(G, H, lay->perm, P.n, P.r, L.npad, L.ncols_pad, pl.part[0], pl.part[1],
-                         pl.part[2]);
+                    s>>>(G, H, lay->perm, P.n, P.r, ncols, L.npad, L.ncols_pad, pl.part[0],
+                         pl.part[1], pl.part[2]);
   TBLR_TRY(launch_status("split_gh_kernel"));
   tau_to_f32<<<(unsigned)std::min<int64_t>(cdiv(P.b * P.b, 256), 1024), 256, 0, s>>>(tau, P.b * P.b,
                                                                                      tf);
@@ -794,9 +798,9 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
   a.ncols = ncols;
   a.ldy = P.r;
   a.y = S;
-  a.split = P.r;
+  a.split = P.r;  // self-adjoint: ncols = r, every column goes to S
   a.ldy2 = P.r;
-  a.y2 = R;
+  a.y2 = P.selfadjoint ? nullptr : R;
   a.tau = tf;
   a.box_of = lay->box_of;
   a.b = (int)P.b;

@@ -20,15 +20,23 @@ __global__ void __launch_bounds__(kThreads) coupling_kernel(Op op, const int32_t
                                                             const int32_t *__restrict__ ranks,
                                                             const double *__restrict__ U,
                                                             const double *__restrict__ V, int k,
-                                                            int b, double *__restrict__ At) {
+                                                            int b, int sym,
+                                                            double *__restrict__ At) {
   extern __shared__ double sm[];
   const int i = blockIdx.x, j = blockIdx.y, tid = threadIdx.x;
+  // Self-adjoint (V = U, A = A^T): CTA (i, j), i < j, also writes Atilde_ji = Atilde_ij^T.
+  if (sym && i > j) return;
+  const bool mirror = sym && i != j;
   const int oi = offsets[i], mi = offsets[i + 1] - oi;
   const int oj = offsets[j], mj = offsets[j + 1] - oj;
   const int ki = ranks[i], kj = ranks[j];
   double *out = At + ((int64_t)i * b + j) * k * k;
+  double *out_t = At + ((int64_t)j * b + i) * k * k;
   if (ki == 0 || kj == 0) {
-    for (int idx = tid; idx < k * k; idx += kThreads) out[idx] = 0.0;
+    for (int idx = tid; idx < k * k; idx += kThreads) {
+      out[idx] = 0.0;
+      if (mirror) out_t[idx] = 0.0;
+    }
     return;
   }
   double *As = sm;                  // [kT][kT + 1]
@@ -88,7 +96,9 @@ __global__ void __launch_bounds__(kThreads) coupling_kernel(Op op, const int32_t
   __syncthreads();
   for (int idx = tid; idx < k * k; idx += kThreads) {
     const int a = idx / k, t = idx % k;
-    out[idx] = (a < ki && t < kj) ? Acc[idx] : 0.0;
+    const double val = (a < ki && t < kj) ? Acc[idx] : 0.0;
+    out[idx] = val;
+    if (mirror) out_t[(int64_t)t * k + a] = val;
   }
 }
 
@@ -195,7 +205,8 @@ extern "C" int tblr_coupling(const tblr_problem *prob, const tblr_layout *lay, c
     auto kern = coupling_kernel<decltype(op)>;
     TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<dim3((unsigned)P.b, (unsigned)P.b), kThreads, smem, s>>>(op, lay->offsets, ranks, u, v,
-                                                                    P.k, (int)P.b, at);
+                                                                    P.k, (int)P.b,
+                                                                    P.selfadjoint ? 1 : 0, at);
     return launch_status("coupling_kernel");
   });
 }

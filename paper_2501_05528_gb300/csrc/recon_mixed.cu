@@ -60,7 +60,7 @@ template <int KERNEL, int KP>
 __global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
     const double *__restrict__ pts, int64_t n, int d, const int32_t *__restrict__ offsets,
     const int32_t *__restrict__ ranks, const double *__restrict__ U, const double *__restrict__ V,
-    int k, int b, double *__restrict__ At) {
+    int k, int b, int sym, double *__restrict__ At) {
   using C = CouplingShape<KP>;
   constexpr int TX = C::TX, RC = C::RC, AT = C::AT, KT = C::KT, AS = C::AS;
   extern __shared__ __align__(16) float sf[];
@@ -72,12 +72,19 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
   // rc[3 * pr + f]: row pair pr's coordinates {xh, yh}, {zh, xl}, {yl, zl}
   float *qs = reinterpret_cast<float *>(rc + 3 * (RC / 2));  // [6][KT] step point coordinates
   const int i = blockIdx.x, j = blockIdx.y, tid = threadIdx.x;
+  // Self-adjoint (V = U, A = A^T): CTA (i, j), i < j, also writes Atilde_ji = Atilde_ij^T.
+  if (sym && i > j) return;
+  const bool mirror = sym && i != j;
   const int oi = offsets[i], mi = offsets[i + 1] - oi;
   const int oj = offsets[j], mj = offsets[j + 1] - oj;
   const int ki = ranks[i], kj = ranks[j];
   double *out = At + ((int64_t)i * b + j) * k * k;
+  double *out_t = At + ((int64_t)j * b + i) * k * k;
   if (ki == 0 || kj == 0) {
-    for (int idx = tid; idx < k * k; idx += kThreads) out[idx] = 0.0;
+    for (int idx = tid; idx < k * k; idx += kThreads) {
+      out[idx] = 0.0;
+      if (mirror) out_t[idx] = 0.0;
+    }
     return;
   }
   const int tx = tid % TX, ty = tid / TX;       // W block: rows 8 ty .., columns 4 tx ..
@@ -239,8 +246,11 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
 #pragma unroll
     for (int y = 0; y < AT; ++y) {
       const int a = AT * ta + x, c = AT * tc + y;
-      if (a < k && c < k)
-        out[(int64_t)a * k + c] = (a < ki && c < kj) ? (double)thi[x][y] - (double)tcc[x][y] : 0.0;
+      if (a < k && c < k) {
+        const double val = (a < ki && c < kj) ? (double)thi[x][y] - (double)tcc[x][y] : 0.0;
+        out[(int64_t)a * k + c] = val;
+        if (mirror) out_t[(int64_t)c * k + a] = val;
+      }
     }
 }
 
@@ -498,8 +508,8 @@ int launch_coupling_f32(const Prob &P, const tblr_layout *lay, const double *u, 
   auto kern = coupling_f32_kernel<KERNEL, KP>;
   const size_t smem = coupling_f32_smem_bytes<KP>();
   TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<dim3((unsigned)P.b, (unsigned)P.b), kThreads, smem, s>>>(lay->pts, P.n, P.d, lay->offsets,
-                                                                 ranks, u, v, P.k, (int)P.b, at);
+  kern<<<dim3((unsigned)P.b, (unsigned)P.b), kThreads, smem, s>>>(
+      lay->pts, P.n, P.d, lay->offsets, ranks, u, v, P.k, (int)P.b, P.selfadjoint ? 1 : 0, at);
   return launch_status("coupling_f32_kernel");
 }
 

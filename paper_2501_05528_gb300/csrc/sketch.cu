@@ -296,7 +296,8 @@ extern "C" int tblr_tagged_sketch(const tblr_problem *prob, const tblr_layout *l
   Prob P;
   TBLR_TRY(check_problem(prob, &P));
   TBLR_TRY(check_layout(P, lay));
-  TBLR_REQUIRE(tau && G && H && s_out && r_out, "tau, G, H, s and rr must be non-NULL");
+  TBLR_REQUIRE(tau && G && s_out && (P.selfadjoint || (H && r_out)),
+               "tau, G, s (and, unless self-adjoint, H and rr) must be non-NULL");
   TBLR_REQUIRE(ws != nullptr && ws_bytes >= tblr_tagged_sketch_workspace(prob),
                "tagged sketch workspace too small");
   cudaStream_t s = as_stream(stream);
@@ -306,6 +307,16 @@ extern "C" int tblr_tagged_sketch(const tblr_problem *prob, const tblr_layout *l
   }
   double *x = static_cast<double *>(ws);
   const bool sym = symmetric_kernel(P.kernel);
+  if (P.selfadjoint) {
+    // A = A^T and H = G: R = S, so only S = A' G is formed.
+    gather_gh_kernel<<<(unsigned)std::min<int64_t>(cdiv(P.r * P.n, 256), 152 * 32), 256, 0, s>>>(
+        G, G, lay->perm, P.n, P.r, 1, x);
+    TBLR_TRY(launch_status("gather_gh_kernel"));
+    TagArgs only{tau, lay->box_of, (int)P.b, P.r, P.r, nullptr};
+    return with_operator(P, lay, dense, 0, [&](auto op) {
+      return launch_apply_fp64<decltype(op), true>(op, x, P.n, P.r, s_out, P.r, s, only);
+    });
+  }
   gather_gh_kernel<<<(unsigned)std::min<int64_t>(cdiv(2 * P.r * P.n, 256), 152 * 32), 256, 0, s>>>(
       G, H, lay->perm, P.n, P.r, 2, x);
   TBLR_TRY(launch_status("gather_gh_kernel"));

@@ -19,7 +19,7 @@ TBLR_OK, TBLR_EINVAL, TBLR_ECUDA, TBLR_EUNSUPPORTED, TBLR_EWORKSPACE, TBLR_ETIME
 KERNELS = {"laplace2d": 1, "laplace3d": 2, "dense": 3}
 FP64, MIXED = 0, 1
 NEARFIELD_PROBE, NEARFIELD_EXACT = 0, 1
-SKETCH_BLACKBOX, SKETCH_TAGGED = 0, 1
+SKETCH_BLACKBOX, SKETCH_TAGGED, SKETCH_SELFADJOINT = 0, 1, 2
 
 
 class TblrError(RuntimeError):
@@ -163,13 +163,14 @@ def _dev():
 
 
 def make_problem(d, kernel, n, grid, lo, hi, k, p=10, e=3, precision=FP64,
-                 nearfield=NEARFIELD_PROBE, sketch=SKETCH_BLACKBOX) -> Problem:
+                 nearfield=NEARFIELD_PROBE, sketch=SKETCH_BLACKBOX, selfadjoint=False) -> Problem:
     g = list(grid) + [1] * (3 - len(grid))
     lo3 = list(lo) + [0.0] * (3 - len(lo))
     hi3 = list(hi) + [1.0] * (3 - len(hi))
     kind = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     return Problem(d, kind, n, (ctypes.c_int32 * 3)(*g), (ctypes.c_double * 3)(*lo3),
-                   (ctypes.c_double * 3)(*hi3), k, p, e, precision, nearfield, sketch)
+                   (ctypes.c_double * 3)(*hi3), k, p, e, precision, nearfield,
+                   sketch | (SKETCH_SELFADJOINT if selfadjoint else 0))
 
 
 def tblr_sizes_of(prob: Problem) -> Sizes:
@@ -273,7 +274,8 @@ def tblr_decode(prob, lay, T):
 
 
 def tblr_tagged_sketch(prob, lay, tau, G, H, dense=None):
-    """S, R from the projected tags (TBLR_SKETCH_TAGGED), without forming Y, Z."""
+    """S, R from the projected tags (TBLR_SKETCH_TAGGED), without forming Y, Z.  With the
+    self-adjoint flag only S is formed and R is returned as S."""
     sz = tblr_sizes_of(prob)
     s = torch.empty(prob.n, sz.r, dtype=torch.float64, device=_dev())
     rr = torch.empty_like(s)
@@ -281,7 +283,7 @@ def tblr_tagged_sketch(prob, lay, tau, G, H, dense=None):
     ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=_dev())
     _check(lib().tblr_tagged_sketch(ctypes.byref(prob), lay.ref, _p(dense), _p(tau), _p(G), _p(H),
                                     _p(s), _p(rr), _p(ws), nbytes, _stream()), "tblr_tagged_sketch")
-    return s, rr
+    return (s, s) if prob.sketch & SKETCH_SELFADJOINT else (s, rr)
 
 
 def tblr_combine(prob, lay, yz, z):
@@ -434,7 +436,7 @@ class BatchJob:
         """After tblr_batch_plan: outputs and the full workspace, sized from the plan."""
         sz, dev, n, k = self.sz, _dev(), self.prob.n, self.prob.k
         f64 = dict(dtype=torch.float64, device=dev)
-        tagged = self.prob.sketch == SKETCH_TAGGED       # Y, Z are never formed
+        tagged = bool(self.prob.sketch & SKETCH_TAGGED)   # Y, Z are never formed
         self.out = Compressed(
             yz=torch.empty(1 if tagged else n * sz.sketch_cols, **f64),
             z=torch.empty(sz.b, sz.ell, **f64),

@@ -251,3 +251,43 @@ def test_tagged_sketch_matches_the_black_box_samples(case):
     rep_o = dict(U=res["U"], V=res["V"], At=res["coupling"], B=res["nearfield"])
     err = metrics.ublr_difference(off, nbr, cnt, s3, res["ranks"], rep, rep_o)
     assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("precision,bound", [(0, 1e-10), (1, 1e-6)], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("kind,d,grid,n,k,e", [("laplace2d", 2, (6, 5), 3001, 8, 3),
+                                              ("laplace3d", 3, (4, 4, 3), 4001, 10, 1)])
+def test_selfadjoint_mode_matches_oracle_with_psi_equal_omega(kind, d, grid, n, k, e, precision,
+                                                              bound):
+    """TBLR_SKETCH_SELFADJOINT (A = A^T, H = G): the oracle run with H = G gives R = S, so
+    V = U; the GPU forms S once, copies U to V and the coupling for i <= j only, mirroring
+    Atilde_ji = Atilde_ij^T.  The result must equal the oracle's general algorithm on the
+    same draws."""
+    tb = _tb()
+    pts = inputs.uniform_points(n, d, seed=5 * n)
+    b = int(np.prod(grid))
+    ell = orc.tag_columns(d, e)
+    T, G, _ = inputs.tagging_draws(b, ell, n, k + 10, seed=5 * n + 1)
+    lo, hi = (0.0,) * d, (1.0,) * d
+    ref = orc.reconstruct_tag(pts, grid, lo, hi, kind, T, G, G, k, 10)
+    assert np.allclose(ref["U"], ref["V"], rtol=0, atol=1e-12)     # R = S in the oracle too
+    prob = tb.make_problem(d, kind, n, grid, lo, hi, k, 10, e, precision=precision,
+                           sketch=tb.SKETCH_TAGGED, selfadjoint=True)
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    out = tb.compress(prob, t(pts), t(T), t(G), t(G))
+    torch.cuda.synchronize()
+    u, v, at = out.u.cpu().numpy(), out.v.cpu().numpy(), out.at.cpu().numpy()
+    assert np.array_equal(u, v)
+    mirrored = np.transpose(at, (1, 0, 3, 2))
+    off_diag = ~np.eye(b, dtype=bool)
+    assert np.array_equal(at[off_diag], mirrored[off_diag])     # written once, mirrored
+    tess = ref["tess"]
+    s3 = 3 ** d
+    nbr, cnt = metrics.padded_neighbours(tess["nbrs"], s3)
+    off = tess["offsets"]
+    B = metrics.blocks_from_flat(out.bnear.cpu().numpy(), out.nf_off.cpu().numpy(), nbr, cnt, off, s3)
+    rep = dict(U=u, V=v, At=at, B=B)
+    rep_o = dict(U=ref["U"], V=ref["V"], At=ref["coupling"], B=ref["nearfield"])
+    err = metrics.ublr_difference(off, nbr, cnt, s3, ref["ranks"], rep, rep_o)
+    print(f"self-adjoint {kind} precision={precision}: rel err vs oracle {err:.3e}")
+    assert err <= bound, err
