@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, readable statement of
 what the CUDA library computes.  Only the tests, ``__graft_entry__.smoke()``
 and the benchmark's CPU-baseline leg may import it; the library never does.
 It shares no code with the CUDA path: numpy (and its LAPACK/BLAS) is the only
-dependency, and every quantity is float64.
+dependency, plus scipy's linear-programming solver for the §5.3 aspect-ratio
+minimisation, and every quantity is float64.
 
 Steps, in the paper's order (Table 1, ``reconstruct_tag``):
 
@@ -227,6 +228,56 @@ def decode(T, tess):
     return z, tau, rho
 
 
+def decode_minratio(T, tess):
+    """§5.3: per box, the vector of null(T(N_i, :)) minimising the aspect ratio of
+    eq. aspect_ratio, instead of the projected direction of `decode`.
+
+    With X_i an orthonormal basis of the null space (s columns) and c_j = X_i^T t_j
+    for j in F_i, a null vector X_i a has projected tags c_j^T a.  Reading (the
+    paper optimises over spherical coordinates "over a convex region"): keep the
+    signs sigma_j of `decode`'s projected tags; inside that sign cell the ratio
+    max_j sigma_j c_j^T a / min_j sigma_j c_j^T a is scale invariant and quasi-convex,
+    and its minimum is the linear program
+
+        minimise rho   subject to   1 <= sigma_j c_j^T a <= rho   (j in F_i),
+
+    over (a, rho) in R^(s+1).  z_i = X_i a / ||X_i a|| keeps the sign pattern, so
+    tau_i = T z_i and rho_i = max |tau_i(F_i)| / min |tau_i(F_i)| equals the LP's rho.
+    A one-dimensional null space (s = 1) or an empty far field leaves `decode`'s z.
+    """
+    from scipy.linalg import null_space
+    from scipy.optimize import linprog
+    z0, tau0, rho0 = decode(T, tess)
+    b, ell = T.shape
+    z, tau, rho = z0.copy(), tau0.copy(), rho0.copy()
+    for i in range(b):
+        F = far_field(tess["nbrs"][i], b)
+        if not len(F):
+            continue
+        X = null_space(T[tess["nbrs"][i], :])
+        s_dim = X.shape[1]
+        if s_dim <= 1:
+            continue
+        sigma = np.sign(tau0[i, F])
+        C = (T[F] @ X) * sigma[:, None]
+        m = len(F)
+        A_ub = np.vstack([np.hstack([-C, np.zeros((m, 1))]), np.hstack([C, -np.ones((m, 1))])])
+        b_ub = np.concatenate([-np.ones(m), np.zeros(m)])
+        c = np.zeros(s_dim + 1)
+        c[-1] = 1.0
+        res = linprog(c, A_ub=A_ub, b_ub=b_ub, bounds=[(None, None)] * (s_dim + 1),
+                      method="highs")
+        if res.status != 0:
+            raise RuntimeError(f"aspect-ratio LP failed for box {i}: {res.message}")
+        zi = X @ res.x[:s_dim]
+        zi /= np.linalg.norm(zi)
+        z[i] = zi
+        tau[i] = T @ zi
+        a = np.abs(tau[i, F])
+        rho[i] = a.max() / a.min()
+    return z, tau, rho
+
+
 # -------------------------------------------- combine and col (Algorithm 2, §2.3)
 
 def combine(Y, z, tess, r):
@@ -338,12 +389,13 @@ def nearfield(op, U, At, V, tess, k):
 
 # ------------------------------------------------- reconstruct_tag (Table 1)
 
-def reconstruct_tag(points, grid, lo, hi, kind, T, G, H, k, p=10, dense=None):
+def reconstruct_tag(points, grid, lo, hi, kind, T, G, H, k, p=10, dense=None, zrule="project"):
     """Full compression A ~ U Atilde V^T + B with tagging bases (Table 1, middle column).
 
     ``T`` is b x ell with ell = 3^d + 1 + e; ``G``, ``H`` are N x (k + p) in the
-    original point order.  Returns a dict of every intermediate and output and
-    the matvec counts of the three steps.
+    original point order.  ``zrule`` picks the null vector of each box: "project"
+    (`decode`) or "minratio" (§5.3, `decode_minratio`).  Returns a dict of every
+    intermediate and output and the matvec counts of the three steps.
     """
     tess = tessellate(points, grid, lo, hi)
     r = k + p
@@ -354,7 +406,7 @@ def reconstruct_tag(points, grid, lo, hi, kind, T, G, H, k, p=10, dense=None):
     Y = op.apply(Om)
     Z = op.apply(Ps, adjoint=True)
     mv1 = op.matvecs
-    z, tau, rho = decode(T, tess)
+    z, tau, rho = (decode_minratio if zrule == "minratio" else decode)(T, tess)
     S = combine(Y, z, tess, r)
     R = combine(Z, z, tess, r)
     U, ks = bases(S, tess, k)

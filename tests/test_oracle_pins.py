@@ -427,3 +427,84 @@ def test_planted_mistakes_are_caught(monkeypatch):
         return out
     monkeypatch.setattr(orc, "nearfield", nearfield_sign)
     assert _recovery_error() > 1e-6
+
+
+# ------------------------------------------------ §5.3 aspect-ratio minimisation
+
+def _grid_and_T(d, grid, e, seed):
+    rng = np.random.default_rng(seed)
+    pts = rng.random((64 * int(np.prod(grid)), d))
+    tess = orc.tessellate(pts, grid, (0.0,) * d, (1.0,) * d)
+    T = rng.standard_normal((tess["b"], orc.tag_columns(d, e)))
+    return tess, T
+
+
+@pytest.mark.parametrize("d,grid,e", [(2, (6, 6), 3), (2, (7, 5), 1), (3, (4, 4, 4), 3)])
+def test_minratio_never_worse_and_stays_in_the_null_space(d, grid, e):
+    """§5.3: the optimised vector is a unit null vector of T(N_i, :), its aspect ratio
+    (eq. aspect_ratio) is at most the projected direction's, and equal where the null
+    space is a line."""
+    tess, T = _grid_and_T(d, grid, e, seed=31 + d + e)
+    z0, tau0, rho0 = orc.decode(T, tess)
+    z, tau, rho = orc.decode_minratio(T, tess)
+    for i in range(tess["b"]):
+        N = tess["nbrs"][i]
+        assert abs(np.linalg.norm(z[i]) - 1.0) < 1e-12
+        assert np.abs(T[N] @ z[i]).max() < 1e-12
+        F = orc.far_field(N, tess["b"])
+        a = np.abs(T[F] @ z[i])
+        assert abs(a.max() / a.min() - rho[i]) <= 1e-12 * rho[i]
+        assert rho[i] <= rho0[i] * (1 + 1e-12)
+        if T.shape[1] - len(N) == 1:
+            assert abs(rho[i] - rho0[i]) <= 1e-10 * rho0[i]
+    assert np.nanmean(rho) < np.nanmean(rho0)      # the optimisation does something
+
+
+def test_minratio_matches_brute_force_on_two_dimensional_null_spaces():
+    """With ell - |N_i| = 2 the null vectors are cos(t) x1 + sin(t) x2: a fine sweep of t
+    inside the sign cell of the projected direction never beats the linear program and
+    comes within the sweep's resolution of it."""
+    tess, T = _grid_and_T(2, (7, 7), 1, seed=77)          # ell = 11, interior |N_i| = 9
+    from scipy.linalg import null_space
+    z0, tau0, _ = orc.decode(T, tess)
+    _, _, rho = orc.decode_minratio(T, tess)
+    t = np.linspace(0.0, 2 * np.pi, 200001)
+    checked = 0
+    for i in range(tess["b"]):
+        N = tess["nbrs"][i]
+        if len(N) != 9:
+            continue
+        F = orc.far_field(N, tess["b"])
+        X = null_space(T[N])
+        sigma = np.sign(tau0[i, F])
+        def ratio(tt):
+            sg = ((T[F] @ X) @ np.vstack([np.cos(tt), np.sin(tt)])) * sigma[:, None]
+            r_ = sg.max(axis=0) / sg.min(axis=0)
+            r_[~(sg > 0).all(axis=0)] = np.inf
+            return r_
+        coarse = ratio(t)
+        j = int(np.argmin(coarse))
+        fine = np.linspace(t[max(j - 2, 0)], t[min(j + 2, len(t) - 1)], 200001)
+        best = min(coarse.min(), ratio(fine).min())   # the ratio has a kink at the optimum
+        assert best >= rho[i] * (1 - 1e-9)
+        assert best <= rho[i] * (1 + 1e-7)
+        checked += 1
+    assert checked >= 9
+
+
+def test_minratio_keeps_exact_recovery():
+    """The choice of null vector does not matter for exactness: with the §5.3 vectors an
+    exactly uniform BLR matrix is still reconstructed to roundoff."""
+    grid, per_box, k, e, seed = (4, 4), 64, 8, 3, 140
+    pts, owner = inputs.box_points(grid, per_box, seed)
+    A = inputs.exact_ublr_matrix(owner, k, seed + 1)
+    tess = orc.tessellate(pts, grid, (0.0, 0.0), (1.0, 1.0))
+    T, G, H = inputs.tagging_draws(tess["b"], orc.tag_columns(2, e), len(pts), k + 10, seed + 2)
+    res = orc.reconstruct_tag(pts, grid, (0.0, 0.0), (1.0, 1.0), "dense", T, G, H, k, 10, dense=A,
+                              zrule="minratio")
+    perm = res["tess"]["perm"]
+    As = A[np.ix_(perm, perm)]
+    err = np.linalg.norm(As - orc.assemble(res)) / np.linalg.norm(As)
+    assert err <= 1e-12, err
+    _, _, rho0 = orc.decode(T, tess)
+    assert np.nanmax(res["rho"] / rho0) <= 1 + 1e-12
