@@ -213,7 +213,8 @@ class Runner:
         self.selfadjoint = bool(w.get("selfadjoint"))
         self.prob = tb.make_problem(d, w["kernel"], w["n"], w["grid"], (0.0,) * d, (1.0,) * d,
                                     w["k"], w["p"], w["e"], precision=w.get("precision", 0),
-                                    sketch=w.get("sketch", 0), selfadjoint=self.selfadjoint)
+                                    sketch=w.get("sketch", 0), selfadjoint=self.selfadjoint,
+                                    zrule=w.get("zrule", 0))
         self.sz = tb.tblr_sizes_of(self.prob)
         lay = tb.tblr_tessellate(self.prob, self.pts)
         nf_off, m_max = tb.tblr_nearfield_offsets(self.prob, lay)
@@ -341,7 +342,7 @@ def mixed_vs_fp64(tb, torch, w, run):
     d = w["d"]
     prob64 = tb.make_problem(d, w["kernel"], w["n"], w["grid"], (0.0,) * d, (1.0,) * d, w["k"],
                              w["p"], w["e"], precision=tb.FP64, sketch=tb.SKETCH_TAGGED,
-                             selfadjoint=bool(w.get("selfadjoint")))
+                             selfadjoint=bool(w.get("selfadjoint")), zrule=w.get("zrule", 0))
     ref = tb.compress(prob64, run.pts, run.T, run.G, run.H)
     torch.cuda.synchronize()
     h = lambda t: t.cpu().numpy()
@@ -467,6 +468,7 @@ def run_gpu(args, w):
                        "precision": "fp64" if w.get("precision", 0) == 0 else "mixed",
                        "sketch": ("tagged, self-adjoint (H = G, V = U)" if run.selfadjoint else
                                   "tagged") if run.tagged else "blackbox",
+                       "zrule": "minratio (§5.3 LP)" if w.get("zrule") else "project",
                        "l2": "flushed by a 256 MiB write before every step",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
@@ -480,6 +482,11 @@ def run_gpu(args, w):
         }
         if accuracy is not None:
             result["accuracy"] = accuracy
+        rho = run.out.rho.cpu().numpy()
+        rho = rho[np.isfinite(rho)]
+        if rho.size:  # eq. aspect_ratio over the boxes (§5.1; minimised with --zrule minratio)
+            result["aspect_ratio"] = {"median": float(np.median(rho)), "p90": float(np.percentile(rho, 90)),
+                                      "max": float(rho.max())}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -666,6 +673,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the mixed-vs-FP64 accuracy check of the mixed path")
+    ap.add_argument("--zrule", default="project", choices=["project", "minratio"],
+                    help="null vector of each box: projection (default) or the §5.3 aspect-ratio LP")
     ap.add_argument("--selfadjoint", action="store_true",
                     help="self-adjoint mode (A = A^T, H = G): V = U, half the coupling")
     ap.add_argument("--sketch", default="blackbox", choices=["blackbox", "tagged"],
@@ -683,6 +692,7 @@ def main():
     w = dict(WORKLOADS[args.workload])
     w["precision"] = 1 if args.precision == "mixed" else 0
     w["sketch"] = 1 if args.sketch == "tagged" else 0
+    w["zrule"] = 1 if args.zrule == "minratio" else 0
     if args.selfadjoint:
         if w["sketch"] != 1:
             raise SystemExit("--selfadjoint needs --sketch tagged")

@@ -81,6 +81,14 @@ extern "C" {
  * near field is unchanged.  Needs the tag-factored sketch. */
 #define TBLR_SKETCH_SELFADJOINT 2
 
+/* Choice of the null vector z_i of T(N_i, :) (tblr_decode).
+ * PROJECT: the normalised projection of 1/sqrt(ell) onto the null space.
+ * MINRATIO: §5.3 - the null vector minimising the aspect ratio of eq.
+ *   aspect_ratio inside the PROJECT vector's sign cell on F_i (a per-box
+ *   linear program; boxes with a one-dimensional null space keep PROJECT). */
+#define TBLR_Z_PROJECT  0
+#define TBLR_Z_MINRATIO 1
+
 /* Problem statement: geometry and tessellation, admissibility, rank
  * (Algorithm 2 "Require": a b x b tessellation of a d-dimensional geometry,
  * target rank k; §2.4 oversampling p; §5.3 extra tag columns e). */
@@ -97,6 +105,7 @@ typedef struct {
     int32_t precision;  /* TBLR_FP64 or TBLR_MIXED */
     int32_t nearfield;  /* TBLR_NEARFIELD_PROBE or TBLR_NEARFIELD_EXACT */
     int32_t sketch;     /* TBLR_SKETCH_BLACKBOX or TBLR_SKETCH_TAGGED, optionally | TBLR_SKETCH_SELFADJOINT */
+    int32_t zrule;      /* TBLR_Z_PROJECT or TBLR_Z_MINRATIO */
 } tblr_problem;
 
 /* Sizes that follow from a problem (no device work). */
@@ -216,9 +225,15 @@ int tblr_tagged_sketch(const tblr_problem *prob, const tblr_layout *lay, const d
  * projection of the all-ones direction; eq. tagsubmat), tau_i = T z_i (projected
  * tags), rho_i = max |tau_i(F_i)| / min |tau_i(F_i)| (eq. aspect_ratio; NaN when
  * F_i is empty).  z: [b*ell], tau: [b*b] (tau[i*b + q]), rho: [b].
- * Limits: ell <= 32. */
+ * With prob->zrule = TBLR_Z_MINRATIO each box then solves the §5.3 linear
+ * program (see TBLR_Z_MINRATIO) on the GPU in FP64; a box whose program stops
+ * without an optimum (an iteration cap) keeps the projected vector and is
+ * counted by tblr_decode_lp_failures.  Limits: ell <= 32. */
 int tblr_decode(const tblr_problem *prob, const tblr_layout *lay, const double *T,
                 double *z, double *tau, double *rho, void *stream);
+/* Boxes whose §5.3 program stopped without an optimum since the last call
+ * (synchronises the device, then resets the count). */
+int tblr_decode_lp_failures(unsigned int *count /* host */);
 
 /* ------------------------------ a5: combine (Algorithm 2; eq. projected_tags)
  * S(I_i, :) = sum_j z_ij Y(I_i, j r : (j+1) r), R likewise from Z.

@@ -50,6 +50,9 @@ int check_problem(const tblr_problem *in, Prob *P) {
   P->r = in->k + in->p;
   P->precision = in->precision;
   P->nearfield = in->nearfield;
+  TBLR_REQUIRE(in->zrule == TBLR_Z_PROJECT || in->zrule == TBLR_Z_MINRATIO, "bad zrule %d",
+               in->zrule);
+  P->zrule = in->zrule;
   P->tagged = (in->sketch & TBLR_SKETCH_TAGGED) != 0;
   P->selfadjoint = (in->sketch & TBLR_SKETCH_SELFADJOINT) != 0;
   int s3 = 1;

@@ -16,6 +16,7 @@ void set_error(const char *fmt, ...);
 struct Prob {
   int d, kernel, k, p, e, r, ell, s3, precision, nearfield;
   bool tagged, selfadjoint;  // sketch mode and the self-adjoint flag
+  int zrule;                 // TBLR_Z_PROJECT or TBLR_Z_MINRATIO
   int64_t n, b, C;  // C = ell * r
   int grid[3];
   double lo[3], hi[3];

@@ -9,6 +9,11 @@
 #include "common.cuh"
 
 namespace tblr {
+
+// Boxes whose aspect-ratio LP stopped without an optimum (read and reset by
+// tblr_decode_lp_failures); such boxes keep the projected vector.
+__device__ unsigned int g_lp_failures;
+
 namespace {
 
 // ---------------------------------------------------------------- a4 decode
@@ -71,6 +76,319 @@ __global__ void __launch_bounds__(32 * kDecWarps) decode_kernel(
   amin = warp_min(amin);
   anyfar = __any_sync(0xffffffffu, anyfar);
   if (lane == 0) rho[i] = anyfar ? amax / amin : NAN;
+}
+
+// --------------------------------------- a4 decode, §5.3 aspect-ratio option
+// Per box (one CTA), minimise eq. aspect_ratio over null(T(N_i,:)) inside the
+// sign cell of the projected vector decode_kernel wrote: with X an orthonormal
+// null basis (s vectors) and c_j = sigma_j X t_j (j in F_i, sigma_j the sign of
+// the projected tag), the linear program in x = (a, rho) in R^(s+1)
+//     minimise rho  subject to  L_j: c_j^T a >= 1,  U_j: rho - c_j^T a >= 0.
+// Active-set primal simplex from the projected vector itself (scaled so its
+// smallest projected tag is 1, it is feasible with L_min and U_max active): the
+// direction is minus the objective gradient projected on the null space of the
+// active rows; a blocking constraint joins the active set; at a vertex (or a
+// zero direction) the multipliers y of A_W^T y = e_rho decide optimality, and
+// the most negative one leaves.  The active rows are re-factorised (QR by
+// modified Gram-Schmidt, twice) each iteration - at most 32 x 32.  The
+// constraint values need only t_j^T (X^T a), so c_j is never stored.
+constexpr int kLpThreads = 128;
+constexpr int kLpRows = 32;  // s + 1 <= ell <= 32
+
+__global__ void __launch_bounds__(kLpThreads) minratio_kernel(
+    const double *__restrict__ T, int b, int ell, int s3, const int32_t *__restrict__ nbr,
+    const int32_t *__restrict__ nnbr, int max_iter, double *__restrict__ z,
+    double *__restrict__ tau, double *__restrict__ rho) {
+  __shared__ double Q[kLpRows][32];      // rows of T(N_i, :), then columns of Q of A_W^T
+  __shared__ double X[kLpRows][32];      // orthonormal null basis, X[c][l]
+  __shared__ double Rm[kLpRows][kLpRows];
+  __shared__ double xv[kLpRows], dv[kLpRows], yv[kLpRows], va[32], vd[32];
+  __shared__ double rstep[kLpThreads];
+  __shared__ int rid[kLpThreads], W[kLpRows + 1], nb_ids[kMaxNbr];
+  __shared__ int s_dim, nW, state;  // state: 0 running, 1 optimal, 2 failed
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = nnbr[i];
+  if (nb >= b || nb >= ell) return;  // no far field, or no null space to move in
+  for (int a = tid; a < nb; a += kLpThreads) nb_ids[a] = nbr[(int64_t)i * s3 + a];
+  __syncthreads();
+  auto is_near = [&](int j) {
+    for (int a = 0; a < nb; ++a)
+      if (nb_ids[a] == j) return true;
+    return false;
+  };
+  const double *zi = z + (int64_t)i * ell;
+  const double *taui = tau + (int64_t)i * b;  // decode_kernel's projected tags (signs)
+  // Null basis: warp 0 orthonormalises T(N_i, :)'s rows, then greedily takes the
+  // unit vectors e_k with the largest residual off span(rows, X so far).
+  if (warp == 0) {
+    for (int a = 0; a < nb; ++a) {
+      double val = lane < ell ? T[(int64_t)nb_ids[a] * ell + lane] : 0.0;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int c = 0; c < a; ++c) {
+          const double qc = Q[c][lane];
+          val -= warp_sum(qc * val) * qc;
+        }
+      val /= sqrt(warp_sum(val * val));
+      Q[a][lane] = val;
+      __syncwarp();
+    }
+    int sd = 0;
+    for (int round = 0; round < ell - nb && sd < kLpRows - 1; ++round) {
+      double best = -1.0, bestv = 0.0;
+      for (int k = 0; k < ell; ++k) {
+        double val = lane == k ? 1.0 : 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int c = 0; c < nb; ++c) val -= warp_sum(Q[c][lane] * val) * Q[c][lane];
+          for (int c = 0; c < sd; ++c) val -= warp_sum(X[c][lane] * val) * X[c][lane];
+        }
+        const double nrm = sqrt(warp_sum(val * val));
+        if (nrm > best) {
+          best = nrm;
+          bestv = val;
+        }
+      }
+      if (best < 1e-8) break;
+      X[sd][lane] = bestv / best;
+      ++sd;
+      __syncwarp();
+    }
+    if (lane == 0) s_dim = sd;
+  }
+  __syncthreads();
+  const int sd = s_dim, nv = sd + 1;
+  if (sd <= 1) return;  // a line: the projected vector is already optimal
+  auto sgn = [&](int j) { return taui[j] < 0.0 ? -1.0 : 1.0; };
+  // t_j^T w for an ell-vector w in shared memory.
+  auto tdot = [&](int j, const double *w) {
+    double acc = 0.0;
+    for (int l = 0; l < ell; ++l) acc = fma(T[(int64_t)j * ell + l], w[l], acc);
+    return acc;
+  };
+  // Start: a0 = coordinates of the projected vector, scaled so min_j c_j^T a0 = 1.
+  if (tid < sd) {
+    double acc = 0.0;
+    for (int l = 0; l < ell; ++l) acc = fma(X[tid][l], zi[l], acc);
+    xv[tid] = acc;
+  }
+  __syncthreads();
+  if (tid < ell) {  // va = X^T a
+    double acc = 0.0;
+    for (int c = 0; c < sd; ++c) acc = fma(X[c][tid], xv[c], acc);
+    va[tid] = acc;
+  }
+  __syncthreads();
+  {
+    double lo = INFINITY, hi = -INFINITY;
+    int jlo = INT_MAX, jhi = INT_MAX;
+    for (int j = tid; j < b; j += kLpThreads) {
+      if (is_near(j)) continue;
+      const double cj = sgn(j) * tdot(j, va);
+      if (cj < lo) lo = cj, jlo = j;
+      if (cj > hi) hi = cj, jhi = j;
+    }
+    rstep[tid] = lo;
+    rid[tid] = jlo;
+    __syncthreads();
+    if (tid == 0) {
+      double best = INFINITY;
+      int bid = INT_MAX;
+      for (int t = 0; t < kLpThreads; ++t)
+        if (rstep[t] < best || (rstep[t] == best && rid[t] < bid)) best = rstep[t], bid = rid[t];
+      yv[0] = best;
+      W[0] = bid;
+    }
+    __syncthreads();
+    rstep[tid] = -hi;
+    rid[tid] = jhi;
+    __syncthreads();
+    if (tid == 0) {
+      double best = INFINITY;
+      int bid = INT_MAX;
+      for (int t = 0; t < kLpThreads; ++t)
+        if (rstep[t] < best || (rstep[t] == best && rid[t] < bid)) best = rstep[t], bid = rid[t];
+      yv[1] = -best;
+      W[1] = b + bid;
+      nW = 2;
+      state = 0;
+    }
+    __syncthreads();
+    const double scale = 1.0 / yv[0];
+    if (tid < sd) xv[tid] *= scale;
+    if (tid == 0) xv[sd] = yv[1] * scale;
+    __syncthreads();
+  }
+  const double tol_y = 1e-12, tol_d = 1e-11;
+  int iter = 0;
+  for (; iter < max_iter; ++iter) {
+    // QR of A_W^T (columns = active rows) by warp 0: lane = component (nv <= 32).
+    if (warp == 0) {
+      int w = nW;
+      bool dropped = false;
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        for (int c = 0; c < w; ++c) {
+          const int id = W[c];
+          const int j = id < b ? id : id - b;
+          double row;  // component `lane` of the active row
+          if (lane < sd) {
+            double acc = 0.0;
+            for (int l = 0; l < ell; ++l) acc = fma(X[lane][l], T[(int64_t)j * ell + l], acc);
+            row = (id < b ? 1.0 : -1.0) * sgn(j) * acc;
+          } else {
+            row = lane == sd ? (id < b ? 0.0 : 1.0) : 0.0;
+          }
+          double val = row;
+          for (int k = 0; k < c; ++k) Rm[k][c] = 0.0;
+          for (int pass = 0; pass < 2; ++pass)
+            for (int k = 0; k < c; ++k) {
+              const double h = warp_sum(Q[k][lane] * val);
+              if (lane == 0) Rm[k][c] += h;
+              val -= h * Q[k][lane];
+            }
+          const double nrm = sqrt(warp_sum(val * val));
+          if (lane == 0) Rm[c][c] = nrm;
+          Q[c][lane] = nrm > 0.0 ? val / nrm : 0.0;
+          __syncwarp();
+        }
+        // Direction: d = -(e_rho - Q Q^T e_rho), minus the objective gradient
+        // projected on the null space of the active rows.
+        double dcomp = lane == sd ? -1.0 : 0.0;
+        for (int k = 0; k < w; ++k) dcomp += Q[k][sd] * Q[k][lane];
+        const double dn = sqrt(warp_sum(dcomp * dcomp));
+        if (w < nv && dn > tol_d) {
+          if (lane < nv) dv[lane] = dcomp;
+          break;
+        }
+        if (dropped) {  // a drop left no descent direction: degenerate, stop here
+          if (lane == 0) state = 2;
+          break;
+        }
+        // Multipliers: R y = Q^T e_rho (back substitution on lane 0).
+        const double qe = lane < w ? Q[lane][sd] : 0.0;
+        if (lane < w) yv[lane] = qe;
+        __syncwarp();
+        if (lane == 0) {
+          for (int c = w - 1; c >= 0; --c) {
+            double acc = yv[c];
+            for (int k = c + 1; k < w; ++k) acc -= Rm[c][k] * yv[k];
+            yv[c] = acc / Rm[c][c];
+          }
+        }
+        __syncwarp();
+        int q = -1;
+        double ymin = -tol_y;
+        for (int c = 0; c < w; ++c)
+          if (yv[c] < ymin) ymin = yv[c], q = c;
+        if (q < 0) {  // all multipliers non-negative: optimal
+          if (lane == 0) state = 1;
+          break;
+        }
+        if (lane == 0) {
+          for (int c = q; c + 1 < w; ++c) W[c] = W[c + 1];
+          nW = w - 1;
+        }
+        __syncwarp();
+        w -= 1;
+        dropped = true;
+      }
+    }
+    __syncthreads();
+    if (state != 0) break;
+    // Ratio test along d over the inactive constraints.
+    if (tid < ell) {
+      double a1 = 0.0, a2 = 0.0;
+      for (int c = 0; c < sd; ++c) {
+        a1 = fma(X[c][tid], xv[c], a1);
+        a2 = fma(X[c][tid], dv[c], a2);
+      }
+      va[tid] = a1;
+      vd[tid] = a2;
+    }
+    __syncthreads();
+    double dnorm = 0.0;
+    for (int c = 0; c < nv; ++c) dnorm = fma(dv[c], dv[c], dnorm);
+    dnorm = sqrt(dnorm);
+    double best = INFINITY;
+    int bid = INT_MAX;
+    for (int j = tid; j < b; j += kLpThreads) {
+      if (is_near(j)) continue;
+      const double sg = sgn(j);
+      const double cx = sg * tdot(j, va), cd = sg * tdot(j, vd);
+      // L_j: slack c^T a - 1, rate c^T d;  U_j: slack rho - c^T a, rate d_rho - c^T d.
+      const double sl[2] = {cx - 1.0, xv[sd] - cx}, rt[2] = {cd, dv[sd] - cd};
+      for (int h = 0; h < 2; ++h) {
+        const int id = h == 0 ? j : b + j;
+        bool active = false;
+        for (int c = 0; c < nW; ++c) active |= W[c] == id;
+        if (active || rt[h] >= -1e-14 * dnorm) continue;
+        const double step = fmax(sl[h], 0.0) / -rt[h];
+        if (step < best || (step == best && id < bid)) best = step, bid = id;
+      }
+    }
+    rstep[tid] = best;
+    rid[tid] = bid;
+    __syncthreads();
+    if (tid == 0) {
+      double bs = INFINITY;
+      int bi = INT_MAX;
+      for (int t = 0; t < kLpThreads; ++t)
+        if (rstep[t] < bs || (rstep[t] == bs && rid[t] < bi)) bs = rstep[t], bi = rid[t];
+      if (bi == INT_MAX || nW >= kLpRows) {
+        state = 2;  // unbounded cannot happen (rho >= 1); keep the projected vector
+      } else {
+        for (int c = 0; c < nv; ++c) xv[c] += bs * dv[c];
+        W[nW] = bi;
+        nW = nW + 1;
+      }
+    }
+    __syncthreads();
+    if (state != 0) break;
+  }
+  if (state != 1) {  // keep the projected vector and count the failure
+    if (tid == 0) atomicAdd(&g_lp_failures, 1u);
+    return;
+  }
+  // z = X^T a / ||X^T a||, then its projected tags and aspect ratio.
+  if (tid < ell) {
+    double acc = 0.0;
+    for (int c = 0; c < sd; ++c) acc = fma(X[c][tid], xv[c], acc);
+    va[tid] = acc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double nn = 0.0;
+    for (int l = 0; l < ell; ++l) nn = fma(va[l], va[l], nn);
+    yv[0] = 1.0 / sqrt(nn);
+  }
+  __syncthreads();
+  if (tid < ell) {
+    va[tid] *= yv[0];
+    z[(int64_t)i * ell + tid] = va[tid];
+  }
+  __syncthreads();
+  double amax = 0.0, amin = INFINITY;
+  for (int j = tid; j < b; j += kLpThreads) {
+    const double t = tdot(j, va);
+    tau[(int64_t)i * b + j] = t;
+    if (!is_near(j)) {
+      amax = fmax(amax, fabs(t));
+      amin = fmin(amin, fabs(t));
+    }
+  }
+  amax = warp_max(amax);
+  amin = warp_min(amin);
+  if (lane == 0) {
+    rstep[warp] = amax;
+    rstep[4 + warp] = amin;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double gmax = 0.0, gmin = INFINITY;
+    for (int w = 0; w < kLpThreads / 32; ++w) {
+      gmax = fmax(gmax, rstep[w]);
+      gmin = fmin(gmin, rstep[4 + w]);
+    }
+    rho[i] = gmax / gmin;
+  }
 }
 
 // --------------------------------------------------------------- a5 combine
@@ -414,7 +732,22 @@ extern "C" int tblr_decode(const tblr_problem *prob, const tblr_layout *lay, con
   TBLR_REQUIRE(P.ell <= 32, "tag decode supports ell <= 32 (got %d)", P.ell);
   decode_kernel<<<(unsigned)cdiv(P.b, kDecWarps), 32 * kDecWarps, 0, as_stream(stream)>>>(
       T, (int)P.b, P.ell, P.s3, lay->nbr, lay->nnbr, z, tau, rho);
-  return launch_status("decode_kernel");
+  TBLR_TRY(launch_status("decode_kernel"));
+  if (P.zrule != TBLR_Z_MINRATIO) return TBLR_OK;
+  // §5.3: minimise the aspect ratio inside the projected vector's sign cell.
+  const int max_iter = 16 * P.ell + 200;
+  minratio_kernel<<<(unsigned)P.b, kLpThreads, 0, as_stream(stream)>>>(
+      T, (int)P.b, P.ell, P.s3, lay->nbr, lay->nnbr, max_iter, z, tau, rho);
+  return launch_status("minratio_kernel");
+}
+
+extern "C" int tblr_decode_lp_failures(unsigned int *count) {
+  TBLR_REQUIRE(count != nullptr, "count is NULL");
+  unsigned int zero = 0;
+  TBLR_CUDA(cudaDeviceSynchronize());
+  TBLR_CUDA(cudaMemcpyFromSymbol(count, tblr::g_lp_failures, sizeof(unsigned int)));
+  TBLR_CUDA(cudaMemcpyToSymbol(tblr::g_lp_failures, &zero, sizeof(unsigned int)));
+  return TBLR_OK;
 }
 
 extern "C" int tblr_combine(const tblr_problem *prob, const tblr_layout *lay, const double *yz,

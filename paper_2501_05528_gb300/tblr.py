@@ -20,6 +20,7 @@ KERNELS = {"laplace2d": 1, "laplace3d": 2, "dense": 3}
 FP64, MIXED = 0, 1
 NEARFIELD_PROBE, NEARFIELD_EXACT = 0, 1
 SKETCH_BLACKBOX, SKETCH_TAGGED, SKETCH_SELFADJOINT = 0, 1, 2
+Z_PROJECT, Z_MINRATIO = 0, 1
 
 
 class TblrError(RuntimeError):
@@ -34,7 +35,8 @@ class Problem(ctypes.Structure):
                 ("grid", ctypes.c_int32 * 3), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("k", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("e", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("nearfield", ctypes.c_int32), ("sketch", ctypes.c_int32)]
+                ("nearfield", ctypes.c_int32), ("sketch", ctypes.c_int32),
+                ("zrule", ctypes.c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -105,6 +107,7 @@ _SIGNATURES = {
                                           _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
     "tblr_release_device_cache": (ctypes.c_int, []),
     "tblr_device_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
+    "tblr_decode_lp_failures": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "tblr_batch_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Job), _VP]),
     "tblr_batch_run": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Job), ctypes.c_int, _VP]),
     "tblr_graph_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Job), ctypes.c_int, _VP,
@@ -163,14 +166,15 @@ def _dev():
 
 
 def make_problem(d, kernel, n, grid, lo, hi, k, p=10, e=3, precision=FP64,
-                 nearfield=NEARFIELD_PROBE, sketch=SKETCH_BLACKBOX, selfadjoint=False) -> Problem:
+                 nearfield=NEARFIELD_PROBE, sketch=SKETCH_BLACKBOX, selfadjoint=False,
+                 zrule=Z_PROJECT) -> Problem:
     g = list(grid) + [1] * (3 - len(grid))
     lo3 = list(lo) + [0.0] * (3 - len(lo))
     hi3 = list(hi) + [1.0] * (3 - len(hi))
     kind = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     return Problem(d, kind, n, (ctypes.c_int32 * 3)(*g), (ctypes.c_double * 3)(*lo3),
                    (ctypes.c_double * 3)(*hi3), k, p, e, precision, nearfield,
-                   sketch | (SKETCH_SELFADJOINT if selfadjoint else 0))
+                   sketch | (SKETCH_SELFADJOINT if selfadjoint else 0), zrule)
 
 
 def tblr_sizes_of(prob: Problem) -> Sizes:
@@ -322,6 +326,13 @@ def tblr_nearfield(prob, lay, u, at, v, ranks, nf_off, m_max: int, total: int, d
                                 _p(ranks), _p(nf_off), m_max, _p(bnear), _p(ws), nbytes, _stream()),
            "tblr_nearfield")
     return bnear
+
+
+def tblr_decode_lp_failures() -> int:
+    """Synchronise the device; return and reset the count of §5.3 programs without an optimum."""
+    out = ctypes.c_uint(0)
+    _check(lib().tblr_decode_lp_failures(ctypes.byref(out)), "tblr_decode_lp_failures")
+    return int(out.value)
 
 
 def tblr_device_timeouts() -> int:

@@ -291,3 +291,44 @@ def test_selfadjoint_mode_matches_oracle_with_psi_equal_omega(kind, d, grid, n, 
     err = metrics.ublr_difference(off, nbr, cnt, s3, ref["ranks"], rep, rep_o)
     print(f"self-adjoint {kind} precision={precision}: rel err vs oracle {err:.3e}")
     assert err <= bound, err
+
+
+@pytest.mark.parametrize("d,grid,n,k,e", [(2, (6, 6), 3001, 8, 3), (2, (7, 5), 2500, 6, 1),
+                                         (3, (4, 4, 4), 4001, 8, 3)])
+def test_minratio_decode_and_compression_match_oracle(d, grid, n, k, e):
+    """TBLR_Z_MINRATIO (§5.3): the per-box LP on the GPU reaches the oracle's optimum
+    (aspect ratios to 1e-9, the same null vectors), and the whole compression with those
+    vectors matches the oracle's to the FP64 bound."""
+    tb = _tb()
+    kind = "laplace2d" if d == 2 else "laplace3d"
+    pts = inputs.uniform_points(n, d, seed=9 * n)
+    b = int(np.prod(grid))
+    T, G, H = inputs.tagging_draws(b, orc.tag_columns(d, e), n, k + 10, seed=9 * n + 1)
+    lo, hi = (0.0,) * d, (1.0,) * d
+    ref = orc.reconstruct_tag(pts, grid, lo, hi, kind, T, G, H, k, 10, zrule="minratio")
+    _, _, rho0 = orc.decode(T, ref["tess"])
+    prob = tb.make_problem(d, kind, n, grid, lo, hi, k, 10, e, zrule=tb.Z_MINRATIO)
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    lay = tb.tblr_tessellate(prob, t(pts))
+    z, tau, rho = tb.tblr_decode(prob, lay, t(T))
+    z, tau, rho = z.cpu().numpy(), tau.cpu().numpy(), rho.cpu().numpy()
+    assert tb.tblr_decode_lp_failures() == 0
+    fin = np.isfinite(ref["rho"])
+    assert np.array_equal(np.isfinite(rho), fin)
+    assert np.max(np.abs(rho[fin] - ref["rho"][fin]) / ref["rho"][fin]) <= 1e-9
+    assert np.nanmean(rho) < np.nanmean(rho0)
+    assert np.max(np.abs(z - ref["z"])) <= 1e-8
+    out = tb.compress(prob, t(pts), t(T), t(G), t(H))
+    torch.cuda.synchronize()
+    tess = ref["tess"]
+    s3 = 3 ** d
+    nbr, cnt = metrics.padded_neighbours(tess["nbrs"], s3)
+    off = tess["offsets"]
+    B = metrics.blocks_from_flat(out.bnear.cpu().numpy(), out.nf_off.cpu().numpy(), nbr, cnt, off, s3)
+    rep = dict(U=out.u.cpu().numpy(), V=out.v.cpu().numpy(), At=out.at.cpu().numpy(), B=B)
+    rep_o = dict(U=ref["U"], V=ref["V"], At=ref["coupling"], B=ref["nearfield"])
+    err = metrics.ublr_difference(off, nbr, cnt, s3, ref["ranks"], rep, rep_o)
+    print(f"minratio d={d} e={e}: mean rho {np.nanmean(rho):.3f} (projected {np.nanmean(rho0):.3f}), "
+          f"reconstruction rel err {err:.3e}")
+    assert err <= 1e-10, err
