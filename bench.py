@@ -236,6 +236,8 @@ class Runner:
         skb = (tb.lib().tblr_tagged_sketch_workspace if self.tagged else
                tb.lib().tblr_sketch_workspace)(tb.ctypes.byref(self.prob))
         self.skws = torch.empty(max(1, skb), dtype=torch.uint8, device=dev)
+        self.cplws = torch.empty(max(1, tb.lib().tblr_coupling_workspace(tb.ctypes.byref(self.prob))),
+                                 dtype=torch.uint8, device=dev)
         self.nfws = torch.empty(tb.lib().tblr_nearfield_workspace(tb.ctypes.byref(self.prob),
                                                                   self.m_max),
                                 dtype=torch.uint8, device=dev)
@@ -247,6 +249,7 @@ class Runner:
         # sketch (1 FP64 gather + 1, or 3 splits + 1 in mixed)
         mixed = w.get("precision", 0) == 1
         base = 4 + 2 + 2 + 1 + 2 + 1 + (1 if mixed else 0)
+        base += (2 if self.selfadjoint else 3) if mixed else 0   # coupling operand conversions
         self.launches_per_step = base + ((4 if mixed else 2) if self.tagged else
                                          (5 if mixed else 3)) - (1 if self.selfadjoint else 0)
 
@@ -289,8 +292,8 @@ class Runner:
         else:
             ck(L.tblr_col(P, lay.ref, p(self.R), p(o.v), p(o.ranks), p(self.colws),
                           self.colws.numel(), s), "col V")
-        ck(L.tblr_coupling(P, lay.ref, None, p(o.u), p(o.v), p(o.ranks), m_max, p(o.at), s),
-           "coupling")
+        ck(L.tblr_coupling(P, lay.ref, None, p(o.u), p(o.v), p(o.ranks), m_max, p(o.at),
+                           p(self.cplws), self.cplws.numel(), s), "coupling")
         ck(L.tblr_nearfield(P, lay.ref, None, p(o.u), p(o.at), p(o.v), p(o.ranks), p(o.nf_off),
                             m_max, p(o.bnear), p(self.nfws), self.nfws.numel(), s), "nearfield")
 

@@ -261,10 +261,13 @@ int tblr_col(const tblr_problem *prob, const tblr_layout *lay, const double *s,
  * FP32 pipes (double-float coordinates, chunked and compensated sums, ~1e-7
  * relative).  With TBLR_SKETCH_SELFADJOINT the caller passes v = u (A = A^T)
  * and only i <= j are formed, Atilde_ji = Atilde_ij^T.
+ * ws: tblr_coupling_workspace bytes (0 for FP64; with TBLR_MIXED the FP32
+ * copies of U, V and the double-float coordinates), 256-byte aligned.
  * Limits: k <= 64; mixed: m_max <= ~780. */
+size_t tblr_coupling_workspace(const tblr_problem *prob);
 int tblr_coupling(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
                   const double *u, const double *v, const int32_t *ranks, int32_t m_max,
-                  double *at, void *stream);
+                  double *at, void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------ a8: near field (Table 1 step 3; §6.1 eq. sparse_struct_ids)
  * For every neighbour pair (i, j = nbr[i*S3+s]) writes B_ij (m_i x m_j,

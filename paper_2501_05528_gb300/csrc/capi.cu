@@ -10,7 +10,7 @@ using namespace tblr;
 namespace {
 
 struct WsPlan {
-  size_t omega, s, r, col, sketch, nf, total;
+  size_t omega, s, r, col, sketch, cpl, nf, total;
 };
 
 WsPlan plan_workspace(const Prob &P, const tblr_problem *prob, int32_t m_max) {
@@ -21,8 +21,9 @@ WsPlan plan_workspace(const Prob &P, const tblr_problem *prob, int32_t m_max) {
   w.r = P.selfadjoint ? 0 : w.s;
   w.col = align256(tblr_col_workspace(prob));
   w.sketch = align256(tagged ? tblr_tagged_sketch_workspace(prob) : tblr_sketch_workspace(prob));
+  w.cpl = align256(tblr_coupling_workspace(prob));
   w.nf = align256(tblr_nearfield_workspace(prob, m_max));
-  w.total = w.omega + w.s + w.r + w.col + w.sketch + w.nf;
+  w.total = w.omega + w.s + w.r + w.col + w.sketch + w.cpl + w.nf;
   return w;
 }
 
@@ -55,7 +56,8 @@ extern "C" int tblr_compress(const tblr_problem *prob, const tblr_layout *lay, c
   double *R = reinterpret_cast<double *>(base + w.omega + w.s);
   char *colws = base + w.omega + w.s + w.r;
   char *skws = colws + w.col;
-  char *nfws = skws + w.sketch;
+  char *cplws = skws + w.sketch;
+  char *nfws = cplws + w.cpl;
   // Step I (Algorithm 2): test matrices, sketch, decode, combine, col.  The
   // tag-factored sketch decodes first and forms S and R without Y and Z.
   if (tagged) {
@@ -76,7 +78,7 @@ extern "C" int tblr_compress(const tblr_problem *prob, const tblr_layout *lay, c
     TBLR_TRY(tblr_col(prob, lay, R, v, ranks, colws, w.col, stream));
   }
   // Step II (Table 1): Atilde = U^T (A V).
-  TBLR_TRY(tblr_coupling(prob, lay, dense, u, v, ranks, m_max, at, stream));
+  TBLR_TRY(tblr_coupling(prob, lay, dense, u, v, ranks, m_max, at, cplws, w.cpl, stream));
   // Step III (Table 1): near field from the identity probes.
   return tblr_nearfield(prob, lay, dense, u, at, v, ranks, nf_off, m_max, bnear, nfws, w.nf, stream);
 }

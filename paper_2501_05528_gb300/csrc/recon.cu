@@ -188,9 +188,17 @@ __global__ void __launch_bounds__(kThreads) nf_block_kernel(
 
 using namespace tblr;
 
+extern "C" size_t tblr_coupling_workspace(const tblr_problem *prob) {
+  Prob P;
+  if (check_problem(prob, &P) != TBLR_OK) return 0;
+  return (P.precision == TBLR_MIXED && symmetric_kernel(P.kernel)) ? coupling_mixed_workspace(P)
+                                                                    : 0;
+}
+
 extern "C" int tblr_coupling(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
                              const double *u, const double *v, const int32_t *ranks,
-                             int32_t m_max, double *at, void *stream) {
+                             int32_t m_max, double *at, void *ws, size_t ws_bytes,
+                             void *stream) {
   Prob P;
   TBLR_TRY(check_problem(prob, &P));
   TBLR_TRY(check_layout(P, lay));
@@ -198,8 +206,11 @@ extern "C" int tblr_coupling(const tblr_problem *prob, const tblr_layout *lay, c
   TBLR_REQUIRE(P.k <= kKMax, "coupling supports k <= %d", kKMax);
   TBLR_REQUIRE(m_max >= 0, "m_max must be >= 0");
   cudaStream_t s = as_stream(stream);
-  if (P.precision == TBLR_MIXED && symmetric_kernel(P.kernel))
-    return coupling_mixed(P, lay, u, v, ranks, at, m_max, s);
+  if (P.precision == TBLR_MIXED && symmetric_kernel(P.kernel)) {
+    TBLR_REQUIRE(ws != nullptr && ws_bytes >= coupling_mixed_workspace(P),
+                 "coupling workspace too small");
+    return coupling_mixed(P, lay, u, v, ranks, at, m_max, ws, s);
+  }
   const size_t smem = sizeof(double) * (kT * (kT + 1) + 3 * kT * P.k + P.k * P.k);
   return with_operator(P, lay, dense, 0, [&](auto op) {
     auto kern = coupling_kernel<decltype(op)>;

@@ -58,9 +58,10 @@ size_t coupling_f32_smem_bytes() {
 
 template <int KERNEL, int KP>
 __global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
-    const double *__restrict__ pts, int64_t n, int d, const int32_t *__restrict__ offsets,
-    const int32_t *__restrict__ ranks, const double *__restrict__ U, const double *__restrict__ V,
-    int k, int b, int sym, double *__restrict__ At) {
+    const float *__restrict__ ch, const float *__restrict__ cl, int64_t npad,
+    const int32_t *__restrict__ offsets, const int32_t *__restrict__ ranks,
+    const float *__restrict__ U, const float *__restrict__ V, int k, int b, int sym,
+    double *__restrict__ At) {
   using C = CouplingShape<KP>;
   constexpr int TX = C::TX, RC = C::RC, AT = C::AT, KT = C::KT, AS = C::AS;
   extern __shared__ __align__(16) float sf[];
@@ -106,8 +107,8 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
         const int r = r0 + 2 * pr + u;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-          h[u][ax] = l[u][ax] = 0.f;
-          if (ax < d && r < mi) split_coord(pts[ax * n + oi + r], h[u][ax], l[u][ax]);
+          h[u][ax] = r < mi ? ch[ax * npad + oi + r] : 0.f;
+          l[u][ax] = r < mi ? cl[ax * npad + oi + r] : 0.f;
         }
       }
       rc[3 * pr + 0] = make_float4(h[0][0], h[1][0], h[0][1], h[1][1]);
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
       // a thread's two 16-byte loads then reads a contiguous run across tx.
       for (int idx = tid; idx < KT * KP; idx += kThreads) {
         const int q = idx / KP, c = idx % KP;
-        const float v = (q0 + q < mj && c < kj) ? (float)V[((int64_t)oj + q0 + q) * k + c] : 0.f;
+        const float v = (q0 + q < mj && c < kj) ? V[((int64_t)oj + q0 + q) * k + c] : 0.f;
         const int ctx = c >> 2, half = (c >> 1) & 1, e = c & 1;
         Vd[((q * 2 + half) * TX + ctx) * 2 + e] = make_float2(v, v);
       }
@@ -134,10 +135,9 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
       for (int q = tid; q < KT; q += kThreads) {
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-          float h = 0.f, l = 0.f;
-          if (ax < d && q0 + q < mj) split_coord(pts[ax * n + oj + q0 + q], h, l);
-          qs[ax * KT + q] = -h;
-          qs[(3 + ax) * KT + q] = -l;
+          const bool in = q0 + q < mj;
+          qs[ax * KT + q] = in ? -ch[ax * npad + oj + q0 + q] : 0.f;
+          qs[(3 + ax) * KT + q] = in ? -cl[ax * npad + oj + q0 + q] : 0.f;
         }
       }
       __syncthreads();
@@ -210,8 +210,7 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
       }
     for (int idx = tid; idx < RC * KP; idx += kThreads) {
       const int r = idx / KP, a = idx % KP;
-      Us[r * (KP + 4) + a] =
-          (r0 + r < mi && a < ki) ? (float)U[((int64_t)oi + r0 + r) * k + a] : 0.f;
+      Us[r * (KP + 4) + a] = (r0 + r < mi && a < ki) ? U[((int64_t)oi + r0 + r) * k + a] : 0.f;
     }
     __syncthreads();
     float tacc[AT][AT];
@@ -502,32 +501,79 @@ __global__ void split_all_coords(const double *__restrict__ pts, int64_t n, int6
 
 }  // namespace
 
+struct CouplingWs {
+  float *ch, *cl, *u, *v;
+  int64_t npad;
+};
+
+CouplingWs coupling_ws(const Prob &P, void *ws) {
+  CouplingWs w;
+  w.npad = cdiv(P.n, 64) * 64;
+  char *p = static_cast<char *>(ws);
+  w.ch = reinterpret_cast<float *>(p);
+  p += align256(sizeof(float) * 3 * w.npad);
+  w.cl = reinterpret_cast<float *>(p);
+  p += align256(sizeof(float) * 3 * w.npad);
+  w.u = reinterpret_cast<float *>(p);
+  p += align256(sizeof(float) * P.n * P.k);
+  w.v = reinterpret_cast<float *>(p);
+  return w;
+}
+
+__global__ void to_f32(const double *__restrict__ x, int64_t len, float *__restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 template <int KERNEL, int KP>
-int launch_coupling_f32(const Prob &P, const tblr_layout *lay, const double *u, const double *v,
+int launch_coupling_f32(const Prob &P, const CouplingWs &w, const tblr_layout *lay,
                         const int32_t *ranks, double *at, cudaStream_t s) {
   auto kern = coupling_f32_kernel<KERNEL, KP>;
   const size_t smem = coupling_f32_smem_bytes<KP>();
   TBLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<dim3((unsigned)P.b, (unsigned)P.b), kThreads, smem, s>>>(
-      lay->pts, P.n, P.d, lay->offsets, ranks, u, v, P.k, (int)P.b, P.selfadjoint ? 1 : 0, at);
+      w.ch, w.cl, w.npad, lay->offsets, ranks, w.u, w.v, P.k, (int)P.b, P.selfadjoint ? 1 : 0, at);
   return launch_status("coupling_f32_kernel");
 }
 
 template <int KERNEL>
-int coupling_f32_dispatch(const Prob &P, const tblr_layout *lay, const double *u, const double *v,
+int coupling_f32_dispatch(const Prob &P, const CouplingWs &w, const tblr_layout *lay,
                           const int32_t *ranks, double *at, cudaStream_t s) {
-  if (P.k <= 16) return launch_coupling_f32<KERNEL, 16>(P, lay, u, v, ranks, at, s);
-  if (P.k <= 32) return launch_coupling_f32<KERNEL, 32>(P, lay, u, v, ranks, at, s);
-  return launch_coupling_f32<KERNEL, 64>(P, lay, u, v, ranks, at, s);
+  if (P.k <= 16) return launch_coupling_f32<KERNEL, 16>(P, w, lay, ranks, at, s);
+  if (P.k <= 32) return launch_coupling_f32<KERNEL, 32>(P, w, lay, ranks, at, s);
+  return launch_coupling_f32<KERNEL, 64>(P, w, lay, ranks, at, s);
+}
+
+size_t coupling_mixed_workspace(const Prob &P) {
+  const int64_t npad = cdiv(P.n, 64) * 64;
+  return 2 * align256(sizeof(float) * 3 * npad) + 2 * align256(sizeof(float) * P.n * P.k);
 }
 
 int coupling_mixed(const Prob &P, const tblr_layout *lay, const double *u, const double *v,
-                   const int32_t *ranks, double *at, int mmax, cudaStream_t s) {
+                   const int32_t *ranks, double *at, int mmax, void *ws, cudaStream_t s) {
   (void)mmax;
   TBLR_REQUIRE(P.k <= 64, "mixed coupling supports k <= 64");
+  TBLR_REQUIRE((reinterpret_cast<uintptr_t>(ws) & 255) == 0, "workspace must be 256-byte aligned");
+  // FP32 operands once, instead of an FP64 -> FP32 conversion (on GB300's slow
+  // FP64 pipe) every time a CTA stages a step.
+  const CouplingWs w = coupling_ws(P, ws);
+  split_all_coords<<<(unsigned)std::min<int64_t>(cdiv(3 * w.npad, 256), 4096), 256, 0, s>>>(
+      lay->pts, P.n, w.npad, P.d, w.ch, w.cl);
+  TBLR_TRY(launch_status("split_all_coords"));
+  const unsigned g = (unsigned)std::min<int64_t>(cdiv(P.n * P.k, 256), 152 * 16);
+  to_f32<<<g, 256, 0, s>>>(u, P.n * P.k, w.u);
+  TBLR_TRY(launch_status("to_f32"));
+  const bool same = v == u || P.selfadjoint;  // self-adjoint: the caller passes v = u
+  if (!same) {
+    to_f32<<<g, 256, 0, s>>>(v, P.n * P.k, w.v);
+    TBLR_TRY(launch_status("to_f32"));
+  }
+  CouplingWs wv = w;
+  if (same) wv.v = w.u;
   return P.kernel == TBLR_KERNEL_LAPLACE2D
-             ? coupling_f32_dispatch<TBLR_KERNEL_LAPLACE2D>(P, lay, u, v, ranks, at, s)
-             : coupling_f32_dispatch<TBLR_KERNEL_LAPLACE3D>(P, lay, u, v, ranks, at, s);
+             ? coupling_f32_dispatch<TBLR_KERNEL_LAPLACE2D>(P, wv, lay, ranks, at, s)
+             : coupling_f32_dispatch<TBLR_KERNEL_LAPLACE3D>(P, wv, lay, ranks, at, s);
 }
 
 size_t nearfield_mixed_workspace(const Prob &P, int mmax) {

@@ -96,7 +96,8 @@ _SIGNATURES = {
     "tblr_combine": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP]),
     "tblr_col_workspace": (_SZ, [_PP]),
     "tblr_col": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _SZ, _VP]),
-    "tblr_coupling": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _I32, _VP, _VP]),
+    "tblr_coupling_workspace": (_SZ, [_PP]),
+    "tblr_coupling": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _SZ, _VP]),
     "tblr_nearfield_workspace": (_SZ, [_PP, _I32]),
     "tblr_nearfield": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _SZ,
                                       _VP]),
@@ -313,8 +314,10 @@ def tblr_col(prob, lay, s):
 def tblr_coupling(prob, lay, u, v, ranks, m_max: int, dense=None):
     sz = tblr_sizes_of(prob)
     at = torch.empty(sz.b, sz.b, prob.k, prob.k, dtype=torch.float64, device=_dev())
+    nbytes = lib().tblr_coupling_workspace(ctypes.byref(prob))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=_dev())
     _check(lib().tblr_coupling(ctypes.byref(prob), lay.ref, _p(dense), _p(u), _p(v), _p(ranks),
-                               m_max, _p(at), _stream()), "tblr_coupling")
+                               m_max, _p(at), _p(ws), nbytes, _stream()), "tblr_coupling")
     return at
 
 
