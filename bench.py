@@ -306,6 +306,12 @@ def measured_peak(key, fallback):
         return fallback, "fallback"
 
 
+# DRAM bytes of one sketch launch, per (kernel, workload), from one 1-pass ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it stands; kept in sync with
+# the kernel (remove the entry when the kernel changes).
+SKETCH_TRAFFIC = {("fp64-blackbox", "laplace2d_n65536"): 24849398272 + 623482880}
+
+
 def padded_cols(ncols, tagged):
     """Columns the tensor-core sketch computes for `ncols` outputs: the fewest tiles of at
     most 160 columns, of equal width rounded up to 32 (128 or 160 for the black-box apply)."""
@@ -478,7 +484,10 @@ def run_gpu(args, w):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": run.launches_per_step * args.steps,
-            "roofline": roofline(w, achieved, statistics.mean(sketch_ms), args.traffic,
+            "roofline": roofline(w, achieved, statistics.mean(sketch_ms),
+                                 args.traffic if args.traffic is not None else SKETCH_TRAFFIC.get(
+                                     ("fp64-blackbox" if w.get("precision", 0) == 0 and
+                                      not run.tagged else "other", args.workload)),
                                  tagged=run.tagged, ncols=cols),
             "cpu_baseline": cpu,
             "clocks": sampler.summary(),
