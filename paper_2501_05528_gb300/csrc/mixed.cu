@@ -35,8 +35,10 @@
 
 #include <algorithm>
 
+#include "coupling_tc.cuh"
 #include "kernels_f32.cuh"
 #include "mixed.cuh"
+#include "tc_pipeline.cuh"
 #include "tc_utils.cuh"
 
 namespace tblr {
@@ -53,7 +55,6 @@ constexpr int kGenWarps = 8;
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 32 * (2 + kEpiWarps + kGenWarps);
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitBudget = 1000000000LL;  // clock cycles (~0.5 s) per wait
 constexpr int kTileBytes = MB * 128;             // one BF16 part of an A tile
 constexpr int kSmemLimit = 232448;               // 227 KiB of opt-in shared memory per CTA
 constexpr int kCS = 3;      // slots of staged point data (copied kCS - 1 chunks ahead)
@@ -125,53 +126,16 @@ struct MixedArgs {
 template <class SM>
 __device__ __forceinline__ bool wait_or_abort(SM &S, volatile int *status, uint64_t *bar,
                                               uint32_t parity) {
-  if (tc::mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (true) {
-    if (tc::mbar_try_wait(bar, parity)) return true;
-    if (S.abort || *status) {
-      S.abort = 1;
-      return false;
-    }
-    if (clock64() - t0 > kWaitBudget) {
-      atomicAdd(&g_mixed_timeouts, 1u);
-      *status = 1;
-      S.abort = 1;
-      return false;
-    }
-  }
+  return pipe::wait_or_abort(S, status, bar, parity, &g_mixed_timeouts);
 }
-
-// Warp-uniform bounded wait: lane 0 polls, every lane gets its verdict (so a
-// warp never splits on a timeout), and the warp barrier orders the lanes'
-// later accesses after the observed phase.
 template <class SM>
 __device__ __forceinline__ bool warp_wait(SM &S, volatile int *status, uint64_t *bar,
                                           uint32_t parity) {
-  bool ok = true;
-  if ((threadIdx.x & 31) == 0) ok = wait_or_abort(S, status, bar, parity);
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  __syncwarp();
-  return ok;
+  return pipe::warp_wait(S, status, bar, parity, &g_mixed_timeouts);
 }
-template <class SM>
-__device__ __forceinline__ bool warp_aborted(SM &S) {
-  return __shfl_sync(0xffffffffu, S.abort, 0) != 0;
-}
-
-// Three-way BF16 split of two FP32 values, packed as K-adjacent pairs.  The
-// remainders v - h and (v - h) - m are exact in FP32.
-__device__ __forceinline__ void split3(float v0, float v1, uint32_t &h, uint32_t &m, uint32_t &l) {
-  const __nv_bfloat162 bh = __floats2bfloat162_rn(v0, v1);
-  const float2 fh = __bfloat1622float2(bh);
-  const float r0 = v0 - fh.x, r1 = v1 - fh.y;
-  const __nv_bfloat162 bm = __floats2bfloat162_rn(r0, r1);
-  const float2 fm = __bfloat1622float2(bm);
-  const __nv_bfloat162 bl = __floats2bfloat162_rn(r0 - fm.x, r1 - fm.y);
-  h = *reinterpret_cast<const uint32_t *>(&bh);
-  m = *reinterpret_cast<const uint32_t *>(&bm);
-  l = *reinterpret_cast<const uint32_t *>(&bl);
-}
+using pipe::split3;
+using pipe::split3_fp64;
+using pipe::warp_aborted;
 
 template <int KERNEL, int NBT, bool TAGGED>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -261,13 +225,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c) {
         const uint32_t ph = (c / STAGES) & 1;
         const long long t0 = clock64();
-        while (!tc::mbar_try_wait(&S.full_b[c % STAGES], ph) && clock64() - t0 < kWaitBudget) {
+        while (!tc::mbar_try_wait(&S.full_b[c % STAGES], ph) && clock64() - t0 < pipe::kWaitBudget) {
         }
       }
       for (int c = (pissued > kCS ? pissued - kCS : 0); c < pissued; ++c) {
         const uint32_t ph = (c / kCS) & 1;
         const long long t0 = clock64();
-        while (!tc::mbar_try_wait(&S.cfull[c % kCS], ph) && clock64() - t0 < kWaitBudget) {
+        while (!tc::mbar_try_wait(&S.cfull[c % kCS], ph) && clock64() - t0 < pipe::kWaitBudget) {
         }
       }
     }
@@ -324,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // Every MMA issued so far has finished once `done` completes.
       tc::mma_commit(&S.done);
       const long long t0 = clock64();
-      while (!tc::mbar_try_wait(&S.done, 0) && clock64() - t0 < kWaitBudget) {
+      while (!tc::mbar_try_wait(&S.done, 0) && clock64() - t0 < pipe::kWaitBudget) {
       }
     }
     __syncwarp();
@@ -533,16 +497,6 @@ __global__ void stage_coords_kernel(const double *__restrict__ pts, const int32_
   }
 }
 
-// Three-way BF16 split of an FP64 value (remainders exact in FP64), so
-// |x - h - m - l| <= 2^-24 |x|.
-__device__ __forceinline__ void split3_fp64(double x, __nv_bfloat16 &h, __nv_bfloat16 &m,
-                                            __nv_bfloat16 &l) {
-  h = __double2bfloat16(x);
-  const double r1 = x - (double)__bfloat162float(h);
-  m = __double2bfloat16(r1);
-  l = __double2bfloat16(r1 - (double)__bfloat162float(m));
-}
-
 // X (FP64, K-major [ncols][n]) split into BF16 h/m/l planes [ncols_pad][npad],
 // zero padded.
 __global__ void split_x_kernel(const double *__restrict__ xt, int64_t n, int64_t ncols,
@@ -557,36 +511,9 @@ __global__ void split_x_kernel(const double *__restrict__ xt, int64_t n, int64_t
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    cudaDriverEntryPointQueryResult q;
-    void *p = nullptr;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 int make_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t npad, int64_t rows,
              int box_rows) {
-  auto fn = encode_fn();
-  TBLR_REQUIRE(fn != nullptr, "cuTensorMapEncodeTiled is unavailable");
-  cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)npad * sizeof(__nv_bfloat16)};
-  cuuint32_t box[2] = {KC, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base),
-                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return TBLR_ECUDA;
-  }
-  return TBLR_OK;
+  return pipe::make_plane_map(map, base, npad, rows, box_rows);
 }
 
 // Column tiling of `ncols` outputs: the fewest tiles of at most 160 columns,
@@ -815,5 +742,6 @@ extern "C" int tblr_device_timeouts(unsigned int *count) {
   TBLR_CUDA(cudaDeviceSynchronize());
   TBLR_CUDA(cudaMemcpyFromSymbol(count, tblr::g_mixed_timeouts, sizeof(unsigned int)));
   TBLR_CUDA(cudaMemcpyToSymbol(tblr::g_mixed_timeouts, &zero, sizeof(unsigned int)));
+  *count += tblr::coupling_tc_take_timeouts();
   return TBLR_OK;
 }

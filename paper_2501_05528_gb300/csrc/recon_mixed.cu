@@ -6,6 +6,9 @@
 //   coupling   Atilde_ij = U_i^T (A_ij V_j)                  (§2.5, Table 1 step 2)
 //   nf lowrank M_is = sum_{c in set} Atilde_ic V_c(0:m_j,:)^T  (§6.1 eq. sparse_struct_ids)
 //   nf block   B_ij = sum_{c in set} A(I_i, I_c(0:m_j)) - U_i M_is
+#include <stdlib.h>
+
+#include "coupling_tc.cuh"
 #include "kernels_f32.cuh"
 #include "recon_mixed.cuh"
 
@@ -547,7 +550,18 @@ int coupling_f32_dispatch(const Prob &P, const CouplingWs &w, const tblr_layout 
 
 size_t coupling_mixed_workspace(const Prob &P) {
   const int64_t npad = cdiv(P.n, 64) * 64;
-  return 2 * align256(sizeof(float) * 3 * npad) + 2 * align256(sizeof(float) * P.n * P.k);
+  const size_t simt = 2 * align256(sizeof(float) * 3 * npad) + 2 * align256(sizeof(float) * P.n * P.k);
+  return std::max(simt, coupling_tc_workspace(P));
+}
+
+// The FP32 SIMT coupling instead of the tensor-core one (TBLR_COUPLING_SIMT=1).
+static bool coupling_simt() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = getenv("TBLR_COUPLING_SIMT");
+    v = (e && atoi(e) != 0) ? 1 : 0;
+  }
+  return v == 1;
 }
 
 int coupling_mixed(const Prob &P, const tblr_layout *lay, const double *u, const double *v,
@@ -555,6 +569,9 @@ int coupling_mixed(const Prob &P, const tblr_layout *lay, const double *u, const
   (void)mmax;
   TBLR_REQUIRE(P.k <= 64, "mixed coupling supports k <= 64");
   TBLR_REQUIRE((reinterpret_cast<uintptr_t>(ws) & 255) == 0, "workspace must be 256-byte aligned");
+  const bool same = v == u || P.selfadjoint;  // self-adjoint: the caller passes v = u
+  if (!coupling_simt())
+    return coupling_tc(P, lay, u, same ? u : v, ranks, at, ws, coupling_mixed_workspace(P), s);
   // FP32 operands once, instead of an FP64 -> FP32 conversion (on GB300's slow
   // FP64 pipe) every time a CTA stages a step.
   const CouplingWs w = coupling_ws(P, ws);
@@ -564,7 +581,6 @@ int coupling_mixed(const Prob &P, const tblr_layout *lay, const double *u, const
   const unsigned g = (unsigned)std::min<int64_t>(cdiv(P.n * P.k, 256), 152 * 16);
   to_f32<<<g, 256, 0, s>>>(u, P.n * P.k, w.u);
   TBLR_TRY(launch_status("to_f32"));
-  const bool same = v == u || P.selfadjoint;  // self-adjoint: the caller passes v = u
   if (!same) {
     to_f32<<<g, 256, 0, s>>>(v, P.n * P.k, w.v);
     TBLR_TRY(launch_status("to_f32"));

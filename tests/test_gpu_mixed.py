@@ -126,3 +126,69 @@ def test_mixed_tagged_sketch_every_tile_width(kind, d, grid, n, k):
         assert err < MIXED_BOUND / 4
         row_err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
         assert row_err.max() < MIXED_BOUND
+
+
+# Coupling blocks on the tensor cores: boxes of 130 to 400 points (several
+# 128-row tiles and 64-point chunks, ragged tails), every rank tile (k -> 16,
+# 32, 64 columns), ranks below k and zero, empty boxes, and the self-adjoint
+# mirror.  Columns of U and V past a box's rank hold garbage that must be ignored.
+@pytest.mark.parametrize("kind,d,grid,n,k,hi,selfadjoint", [
+    ("laplace2d", 2, (3, 3), 3001, 6, 1.0, False),
+    ("laplace3d", 3, (2, 2, 2), 2100, 20, 1.0, False),
+    ("laplace2d", 2, (4, 4), 2600, 45, 0.6, False),
+    ("laplace3d", 3, (2, 2, 2), 1500, 64, 1.0, False),
+    ("laplace2d", 2, (3, 3), 3001, 32, 1.0, True),
+    ("laplace3d", 3, (2, 2, 2), 2100, 64, 1.0, True),
+])
+def test_mixed_coupling_matches_dense_definition(kind, d, grid, n, k, hi, selfadjoint):
+    """Atilde_ij = U_i(:, :k_i)^T A(I_i, I_j) V_j(:, :k_j) (§2.5), zero past the ranks."""
+    tb = _tb()
+    rng = np.random.default_rng(1000 + n + k)
+    pts = inputs.uniform_points(n, d, seed=n + k) * hi      # hi < 1 leaves boxes empty
+    lo, top = (0.0,) * d, (1.0,) * d
+    tess = orc.tessellate(pts, grid, lo, top)
+    perm, off = tess["perm"], tess["offsets"]
+    b = len(off) - 1
+    m = np.diff(off)
+    ranks = np.minimum(k, m).astype(np.int32)
+    busy = np.flatnonzero(m > 0)
+    ranks[busy[1]] = max(1, k // 2)
+    ranks[busy[2]] = 0
+    ranks[busy[3]] = 1
+    U = rng.standard_normal((n, k)) / 16
+    V = U if selfadjoint else rng.standard_normal((n, k)) / 16
+    garbage = 1e30
+    U = U.copy()
+    V = V if selfadjoint else V.copy()
+    for i in range(b):
+        U[off[i]:off[i + 1], ranks[i]:] = garbage
+        if not selfadjoint:
+            V[off[i]:off[i + 1], ranks[i]:] = -garbage
+    A = orc.dense_matrix(orc.KernelOperator(kind, pts[perm]))
+    ref = np.zeros((b, b, k, k))
+    for i in range(b):
+        for j in range(b):
+            ki, kj = ranks[i], ranks[j]
+            ref[i, j, :ki, :kj] = (U[off[i]:off[i + 1], :ki].T @ A[off[i]:off[i + 1], off[j]:off[j + 1]]
+                                   @ V[off[j]:off[j + 1], :kj])
+    prob = tb.make_problem(d, kind, n, grid, lo, top, k, 10, 3, precision=tb.MIXED,
+                           sketch=tb.SKETCH_TAGGED, selfadjoint=selfadjoint)
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    lay = tb.tblr_tessellate(prob, t(pts))
+    assert np.array_equal(lay.perm.cpu().numpy(), perm)
+    u_d = t(U)
+    v_d = u_d if selfadjoint else t(V)
+    at = tb.tblr_coupling(prob, lay, u_d, v_d, t(ranks), int(m.max())).cpu().numpy()
+    assert tb.tblr_device_timeouts() == 0
+    for i in range(b):
+        for j in range(b):
+            if ranks[i] == 0 or ranks[j] == 0:
+                assert not at[i, j].any()
+                continue
+            assert not at[i, j, ranks[i]:, :].any() and not at[i, j, :, ranks[j]:].any()
+            blk = np.linalg.norm(at[i, j] - ref[i, j]) / np.linalg.norm(ref[i, j])
+            assert blk < MIXED_BOUND, (i, j, blk)
+    err = metrics.rel(at, ref)
+    print(f"mixed coupling {kind} n={n} k={k} selfadjoint={selfadjoint}: rel err {err:.3e}")
+    assert err < MIXED_BOUND / 4
