@@ -52,7 +52,7 @@ template <int KP>
 struct CplCfg {
   static constexpr int RS = KP + 4;  // row stride of W and U in shared memory (floats)
   static constexpr int kStageBytes = kParts * (kTileBytes + KP * 128);
-  static constexpr int kFixed = 2048 + kCS * kQcBytes + 2 * MB * RS * 4;
+  static constexpr int kFixed = 2048 + kCS * kQcBytes + MB * (RS + KP) * 4;
   static constexpr int STAGES = (kSmemLimit - kFixed) / kStageBytes >= 3 ? 3 : 2;
   static constexpr int AC = KP >= 32 ? 4 : 2;     // Atilde columns per epilogue thread
   static constexpr int AA = KP * KP / (MB * AC);  // Atilde rows per epilogue thread
@@ -80,10 +80,10 @@ struct __align__(1024) CplSmem {
   uint8_t x[STAGES][kParts][KP * 128];    // V_j h, m, l: KP rows x 128 bytes
   float4 qc[kCS][3][4][8];                // chunk coordinates (the mixed apply's layout)
   float w[MB][RS];                        // W of the finished row tile
-  float u[MB][RS];                        // U_i rows of that tile
+  float u[MB][KP];                        // U_i rows of the tile (bulk-copied a tile ahead)
   uint64_t cfull[kCS], cfree[kCS];
   uint64_t full_a[STAGES], full_b[STAGES], empty[STAGES];
-  uint64_t dfull[2], dempty[2], done;
+  uint64_t dfull[2], dempty[2], done, ufull;
   uint32_t tmem_base;
   volatile int abort;
 };
@@ -97,7 +97,9 @@ struct CplArgs {
   const int32_t *offsets;  // b + 1 point offsets of the boxes
   const int32_t *poff;     // b + 1 box-padded offsets (multiples of 64)
   const int32_t *ranks;
-  const float *u;  // U in FP32, n x k
+  // U in FP32 in the box-padded order, rows of KP (zero past the rank and in
+  // padding slots), with MB spare rows at the end.
+  const float *u;
   int k, b, sym;
   double *at;
   volatile int *status;
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&S.cfree[t], kGenWarps);
     }
     tc::mbar_init(&S.done, 1);
+    tc::mbar_init(&S.ufull, 1);
     tc::fence_mbar_init();
     for (int t = 0; t < kParts; ++t) tc::tma_prefetch(&maps.part[t]);
   }
@@ -283,13 +286,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int e = 0; e < NACC; ++e) tacc[e] = 0.f;
     };
     bool ok = !pipe::warp_aborted(S);
+    // U_i rows of row tile tt: one bulk copy of MB rows of KP floats.
+    constexpr uint32_t kUBytes = MB * KP * 4;
+    auto copy_u = [&](int tt) {
+      tc::mbar_arrive_expect_tx(&S.ufull, kUBytes);
+      tc::bulk_load(&S.u[0][0], a.u + (int64_t)(pi + MB * tt) * KP, kUBytes, &S.ufull);
+    };
+    int u_issued = 0;
+    if (et == 0 && ok) copy_u(u_issued++);
     // Every epilogue warp runs all nsteps iterations (skipping waits once a
     // wait failed), so the named barriers below are always reached by all four.
     for (int st = 0; st < nsteps; ++st) {
       const int slot = st & 1, c = st % nch, t = st / nch;
       const bool last = c == nch - 1;
       if (ok && !pipe::warp_wait(S, a.status, &S.dfull[slot], (st >> 1) & 1, timeouts)) ok = false;
-      if (last) epi_sync();  // the previous tile's U^T W has finished reading S.w, S.u
       if (ok) {
         tc::tc_fence_after();
         const uint32_t d_t = tmem + slot * KP + lanes;
@@ -309,6 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             hv[e] = tt;
           }
           if (last) {
+            // W row r of the tile; S.w is free: the previous tile's U^T W
+            // ended with a barrier.
             float4 *wr = reinterpret_cast<float4 *>(&S.w[r][cg * 16]);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
@@ -325,30 +337,57 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) tc::mbar_arrive(&S.dempty[slot]);
       }
       if (last) {
-        // U_i rows of the tile (zero past the box and past rank k_i).
-        const int lr = MB * t + r;
-        const float *urow = a.u + (int64_t)(oi + (lr < mi ? lr : 0)) * k;
-#pragma unroll 4
-        for (int col = 0; col < KP; ++col) S.u[r][col] = (lr < mi && col < ki) ? urow[col] : 0.f;
-        epi_sync();
-        const int rend = min(MB, mi - MB * t);
+        epi_sync();  // W complete
+        if (ok && !pipe::warp_wait(S, a.status, &S.ufull, t & 1, timeouts)) ok = false;
+        if (ok) {
+          // Atilde += U_i(tile)^T W in packed FP32x2 (column pairs of W).
+          const int rend = min(MB, mi - MB * t);
+          float2 tp[NACC / 2];
 #pragma unroll
-        for (int e = 0; e < NACC; ++e) tacc[e] = 0.f;
+          for (int e = 0; e < NACC / 2; ++e) tp[e] = make_float2(0.f, 0.f);
 #pragma unroll 2
-        for (int rr = 0; rr < rend; ++rr) {
-          float uv[AA], wv[AC];
+          for (int rr = 0; rr < rend; ++rr) {
+            float uv[AA];
+            float2 wv[AC / 2];
+            if constexpr (AA % 4 == 0) {
 #pragma unroll
-          for (int x = 0; x < AA; ++x) uv[x] = S.u[rr][AA * ta + x];
+              for (int x = 0; x < AA; x += 4) {
+                const float4 q4 = *reinterpret_cast<const float4 *>(&S.u[rr][AA * ta + x]);
+                uv[x] = q4.x;
+                uv[x + 1] = q4.y;
+                uv[x + 2] = q4.z;
+                uv[x + 3] = q4.w;
+              }
+            } else {
 #pragma unroll
-          for (int y = 0; y < AC; ++y) wv[y] = S.w[rr][AC * tcol + y];
+              for (int x = 0; x < AA; ++x) uv[x] = S.u[rr][AA * ta + x];
+            }
 #pragma unroll
-          for (int x = 0; x < AA; ++x)
+            for (int y = 0; y < AC / 2; ++y)
+              wv[y] = *reinterpret_cast<const float2 *>(&S.w[rr][AC * tcol + 2 * y]);
 #pragma unroll
-            for (int y = 0; y < AC; ++y) tacc[AC * x + y] = fmaf(uv[x], wv[y], tacc[AC * x + y]);
-          if ((rr & (kPiece - 1)) == kPiece - 1 || rr == rend - 1) fold();
+            for (int x = 0; x < AA; ++x)
+#pragma unroll
+              for (int y = 0; y < AC / 2; ++y)
+                tp[x * (AC / 2) + y] =
+                    __ffma2_rn(make_float2(uv[x], uv[x]), wv[y], tp[x * (AC / 2) + y]);
+            if ((rr & (kPiece - 1)) == kPiece - 1 || rr == rend - 1) {
+#pragma unroll
+              for (int e = 0; e < NACC / 2; ++e) {
+                tacc[2 * e] = tp[e].x;
+                tacc[2 * e + 1] = tp[e].y;
+                tp[e] = make_float2(0.f, 0.f);
+              }
+              fold();
+            }
+          }
         }
+        epi_sync();  // S.w and S.u are free again
+        if (et == 0 && ok && t + 1 < ntiles) copy_u(u_issued++);
       }
     }
+    // A U copy still in flight must land before the CTA exits.
+    if (et == 0 && u_issued > 0) pipe::drain(&S.ufull, (u_issued - 1) & 1);
     if (ok) {
       auto emit = [&](int e, float hv, float cv) {
         const int ar = AA * ta + e / AC, ac = AC * tcol + e % AC;
@@ -542,10 +581,21 @@ __global__ void split_v_boxpad_kernel(const double *__restrict__ v,
   }
 }
 
-__global__ void to_f32_kernel(const double *__restrict__ x, int64_t len, float *__restrict__ y) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len;
-       t += (int64_t)gridDim.x * blockDim.x)
-    y[t] = (float)x[t];
+// U in FP32 in the box-padded order, rows of kp floats: column a < rank_i of
+// the box's point in slot t, zero for padding slots and the other columns
+// (the MB spare rows at the end stay unset and are never used).
+__global__ void u_boxpad_kernel(const double *__restrict__ u, const int32_t *__restrict__ offsets,
+                                const int32_t *__restrict__ poff,
+                                const int32_t *__restrict__ ranks, int k, int kp, int b,
+                                float *__restrict__ uf) {
+  for (int jb = blockIdx.x; jb < b; jb += gridDim.x) {
+    const int o = offsets[jb], m = offsets[jb + 1] - o, p0 = poff[jb];
+    const int len = poff[jb + 1] - p0, kj = ranks[jb];
+    for (int idx = threadIdx.x; idx < len * kp; idx += blockDim.x) {
+      const int l = idx / kp, c = idx % kp;
+      uf[(int64_t)(p0 + l) * kp + c] = (l < m && c < kj) ? (float)u[(int64_t)(o + l) * k + c] : 0.f;
+    }
+  }
 }
 
 struct CplLayout {
@@ -561,7 +611,7 @@ CplLayout cpl_layout(const Prob &P) {
   L.head = 256;
   L.coords = align256(sizeof(float4) * 3 * (L.npb / 2));
   L.planes = align256(sizeof(__nv_bfloat16) * L.kp * L.npb);
-  L.uf = align256(sizeof(float) * P.n * P.k);
+  L.uf = align256(sizeof(float) * (L.npb + MB) * L.kp);
   L.poff = align256(sizeof(int32_t) * (P.b + 1));
   L.total = L.head + L.coords + kParts * L.planes + L.uf + L.poff;
   return L;
@@ -616,9 +666,8 @@ int coupling_tc(const Prob &P, const tblr_layout *lay, const double *u, const do
   split_v_boxpad_kernel<<<gb, 256, 0, s>>>(v, lay->offsets, poff, ranks, (int)P.k, L.kp, b, L.npb,
                                            part[0], part[1], part[2]);
   TBLR_TRY(launch_status("split_v_boxpad_kernel"));
-  to_f32_kernel<<<(unsigned)std::min<int64_t>(cdiv(P.n * P.k, 256), 152 * 16), 256, 0, s>>>(
-      u, P.n * P.k, uf);
-  TBLR_TRY(launch_status("to_f32_kernel"));
+  u_boxpad_kernel<<<gb, 256, 0, s>>>(u, lay->offsets, poff, ranks, (int)P.k, L.kp, b, uf);
+  TBLR_TRY(launch_status("u_boxpad_kernel"));
   CplMaps maps;
   for (int t = 0; t < kParts; ++t)
     TBLR_TRY(pipe::make_plane_map(&maps.part[t], part[t], L.npb, L.kp, L.kp));

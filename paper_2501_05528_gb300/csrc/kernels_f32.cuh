@@ -8,6 +8,21 @@
 
 namespace tblr {
 
+// The MUFU approximations (rsqrt.approx, lg2.approx: ~2^-22 relative) with
+// subnormal inputs flushed to zero.  Squared distances of distinct points are
+// never subnormal, and the flushing forms skip the input range scaling that
+// the plain forms carry.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <int KERNEL>
 __device__ __forceinline__ float entry_f32(const float (&ph)[3], const float (&pl)[3],
                                            const float (&qh)[3], const float (&ql)[3]) {
@@ -15,13 +30,13 @@ __device__ __forceinline__ float entry_f32(const float (&ph)[3], const float (&p
     const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
     const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
     const float r2 = fmaf(dx, dx, dy * dy);
-    return 0.34657359027997264f * __log2f(r2);  // 0.5 ln(2) log2(r^2) = log r
+    return 0.34657359027997264f * lg2_ftz(r2);  // 0.5 ln(2) log2(r^2) = log r
   } else {
     const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
     const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
     const float dz = (ph[2] - qh[2]) + (pl[2] - ql[2]);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    return 0.07957747154594767f * rsqrtf(r2);  // 1 / (4 pi r)
+    return 0.07957747154594767f * rsqrt_ftz(r2);  // 1 / (4 pi r)
   }
 }
 
@@ -34,18 +49,18 @@ __device__ __forceinline__ float entry_f32_raw(const float (&ph)[3], const float
   if (KERNEL == TBLR_KERNEL_LAPLACE2D) {
     const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
     const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
-    return __log2f(fmaf(dx, dx, dy * dy));
+    return lg2_ftz(fmaf(dx, dx, dy * dy));
   } else {
     const float dx = (ph[0] - qh[0]) + (pl[0] - ql[0]);
     const float dy = (ph[1] - qh[1]) + (pl[1] - ql[1]);
     const float dz = (ph[2] - qh[2]) + (pl[2] - ql[2]);
-    return rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    return rsqrt_ftz(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
   }
 }
 // The raw entry from the squared distance r2 (FP32).
 template <int KERNEL>
 __device__ __forceinline__ float entry_f32_of_r2(float r2) {
-  return KERNEL == TBLR_KERNEL_LAPLACE2D ? __log2f(r2) : rsqrtf(r2);
+  return KERNEL == TBLR_KERNEL_LAPLACE2D ? lg2_ftz(r2) : rsqrt_ftz(r2);
 }
 template <int KERNEL>
 __host__ __device__ constexpr float entry_f32_factor() {

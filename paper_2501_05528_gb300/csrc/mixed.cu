@@ -222,18 +222,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       // Copies still in flight must land before the CTA exits.
-      for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c) {
-        const uint32_t ph = (c / STAGES) & 1;
-        const long long t0 = clock64();
-        while (!tc::mbar_try_wait(&S.full_b[c % STAGES], ph) && clock64() - t0 < pipe::kWaitBudget) {
-        }
-      }
-      for (int c = (pissued > kCS ? pissued - kCS : 0); c < pissued; ++c) {
-        const uint32_t ph = (c / kCS) & 1;
-        const long long t0 = clock64();
-        while (!tc::mbar_try_wait(&S.cfull[c % kCS], ph) && clock64() - t0 < pipe::kWaitBudget) {
-        }
-      }
+      for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
+        pipe::drain(&S.full_b[c % STAGES], (c / STAGES) & 1);
+      for (int c = (pissued > kCS ? pissued - kCS : 0); c < pissued; ++c)
+        pipe::drain(&S.cfull[c % kCS], (c / kCS) & 1);
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
@@ -287,9 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // Every MMA issued so far has finished once `done` completes.
       tc::mma_commit(&S.done);
-      const long long t0 = clock64();
-      while (!tc::mbar_try_wait(&S.done, 0) && clock64() - t0 < pipe::kWaitBudget) {
-      }
+      pipe::drain(&S.done, 0);
     }
     __syncwarp();
   } else if (warp < 2 + kEpiWarps) {

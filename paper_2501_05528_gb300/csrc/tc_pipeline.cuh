@@ -13,6 +13,7 @@ namespace tblr {
 namespace pipe {
 
 constexpr long long kWaitBudget = 1000000000LL;  // clock cycles (~0.5 s) per wait
+constexpr uint32_t kSleepNs = 200000;            // suspend hint of one try_wait (0.2 ms)
 
 // Waits for phase `parity` of `bar`.  Gives up when another role of the CTA
 // (S.abort) or another CTA of the launch (*status) has given up, or after
@@ -23,7 +24,9 @@ __device__ __forceinline__ bool wait_or_abort(SM &S, volatile int *status, uint6
   if (tc::mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (tc::mbar_try_wait(bar, parity)) return true;
+    // Suspended in the barrier rather than polling, so a waiting role takes
+    // no issue slots from the warps that share its scheduler.
+    if (tc::mbar_try_wait_sleep(bar, parity, kSleepNs)) return true;
     if (S.abort || *status) {
       S.abort = 1;
       return false;
@@ -58,7 +61,7 @@ __device__ __forceinline__ bool warp_aborted(SM &S) {
 // (bounded like every other wait).
 __device__ __forceinline__ void drain(uint64_t *bar, uint32_t parity) {
   const long long t0 = clock64();
-  while (!tc::mbar_try_wait(bar, parity) && clock64() - t0 < kWaitBudget) {
+  while (!tc::mbar_try_wait_sleep(bar, parity, kSleepNs) && clock64() - t0 < kWaitBudget) {
   }
 }
 
