@@ -293,13 +293,77 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::bulk_load(&S.u[0][0], a.u + (int64_t)(pi + MB * tt) * KP, kUBytes, &S.ufull);
     };
     int u_issued = 0;
+    // U_i(tile)^T W of a finished tile is spread over the drain steps of the
+    // next tile ("pieces" of prows rows after a slot has been released), so
+    // the epilogue keeps draining accumulator slots on time.  pend = the tile
+    // whose W sits in S.w (-1: none), prow = its next row; u_tile = the last
+    // tile whose U_i rows were requested into S.u (issued as soon as the
+    // pending reduction no longer reads S.u, one step or more ahead of use).
+    int pend = -1, prow = 0, pend_rows = 0, prows = MB, u_tile = 0;
+    bool u_ready = false;
     if (et == 0 && ok) copy_u(u_issued++);
+    auto reduce_rows = [&](int r_end) {
+      if (!u_ready) {
+        if (ok && !pipe::warp_wait(S, a.status, &S.ufull, pend & 1, timeouts)) ok = false;
+        u_ready = true;
+      }
+      if (ok) {
+        // Atilde += U_i(rows)^T W(rows) in packed FP32x2: pairs of U columns
+        // (Atilde rows) times one W column.
+        float2 tp[NACC / 2];
+#pragma unroll
+        for (int e = 0; e < NACC / 2; ++e) tp[e] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int rr = prow; rr < r_end; ++rr) {
+          float wv[AC];
+#pragma unroll
+          for (int y = 0; y < AC; ++y) wv[y] = S.w[rr][AC * tcol + y];
+          if constexpr (AA % 2 == 0) {
+            float2 up[AA / 2];
+#pragma unroll
+            for (int x = 0; x < AA / 2; ++x)
+              up[x] = *reinterpret_cast<const float2 *>(&S.u[rr][AA * ta + 2 * x]);
+            // tp[(x / 2) * AC + y] holds entries (x, y) and (x + 1, y), x even.
+#pragma unroll
+            for (int x = 0; x < AA / 2; ++x)
+#pragma unroll
+              for (int y = 0; y < AC; ++y)
+                tp[x * AC + y] = __ffma2_rn(up[x], make_float2(wv[y], wv[y]), tp[x * AC + y]);
+          } else {
+            const float uv = S.u[rr][AA * ta];
+#pragma unroll
+            for (int y = 0; y < AC / 2; ++y)
+              tp[y] = __ffma2_rn(make_float2(uv, uv), make_float2(wv[2 * y], wv[2 * y + 1]), tp[y]);
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < NACC / 2; ++e) {
+          if constexpr (AA % 2 == 0) {
+            const int x = 2 * (e / AC), y = e % AC;
+            tacc[AC * x + y] = tp[e].x;
+            tacc[AC * (x + 1) + y] = tp[e].y;
+          } else {
+            tacc[2 * e] = tp[e].x;
+            tacc[2 * e + 1] = tp[e].y;
+          }
+        }
+        fold();
+      }
+      prow = r_end;
+    };
     // Every epilogue warp runs all nsteps iterations (skipping waits once a
     // wait failed), so the named barriers below are always reached by all four.
     for (int st = 0; st < nsteps; ++st) {
       const int slot = st & 1, c = st % nch, t = st / nch;
       const bool last = c == nch - 1;
       if (ok && !pipe::warp_wait(S, a.status, &S.dfull[slot], (st >> 1) & 1, timeouts)) ok = false;
+      if (last && u_tile < t) {
+        // The pending tile's remaining rows; then S.w and S.u are free.
+        if (pend >= 0 && prow < pend_rows) reduce_rows(pend_rows);
+        epi_sync();
+        if (et == 0 && ok) copy_u(u_issued++);  // U_i rows of tile t
+        u_tile = t;
+      }
       if (ok) {
         tc::tc_fence_after();
         const uint32_t d_t = tmem + slot * KP + lanes;
@@ -319,8 +383,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             hv[e] = tt;
           }
           if (last) {
-            // W row r of the tile; S.w is free: the previous tile's U^T W
-            // ended with a barrier.
             float4 *wr = reinterpret_cast<float4 *>(&S.w[r][cg * 16]);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
@@ -337,53 +399,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) tc::mbar_arrive(&S.dempty[slot]);
       }
       if (last) {
-        epi_sync();  // W complete
-        if (ok && !pipe::warp_wait(S, a.status, &S.ufull, t & 1, timeouts)) ok = false;
-        if (ok) {
-          // Atilde += U_i(tile)^T W in packed FP32x2 (column pairs of W).
-          const int rend = min(MB, mi - MB * t);
-          float2 tp[NACC / 2];
-#pragma unroll
-          for (int e = 0; e < NACC / 2; ++e) tp[e] = make_float2(0.f, 0.f);
-#pragma unroll 2
-          for (int rr = 0; rr < rend; ++rr) {
-            float uv[AA];
-            float2 wv[AC / 2];
-            if constexpr (AA % 4 == 0) {
-#pragma unroll
-              for (int x = 0; x < AA; x += 4) {
-                const float4 q4 = *reinterpret_cast<const float4 *>(&S.u[rr][AA * ta + x]);
-                uv[x] = q4.x;
-                uv[x + 1] = q4.y;
-                uv[x + 2] = q4.z;
-                uv[x + 3] = q4.w;
-              }
-            } else {
-#pragma unroll
-              for (int x = 0; x < AA; ++x) uv[x] = S.u[rr][AA * ta + x];
-            }
-#pragma unroll
-            for (int y = 0; y < AC / 2; ++y)
-              wv[y] = *reinterpret_cast<const float2 *>(&S.w[rr][AC * tcol + 2 * y]);
-#pragma unroll
-            for (int x = 0; x < AA; ++x)
-#pragma unroll
-              for (int y = 0; y < AC / 2; ++y)
-                tp[x * (AC / 2) + y] =
-                    __ffma2_rn(make_float2(uv[x], uv[x]), wv[y], tp[x * (AC / 2) + y]);
-            if ((rr & (kPiece - 1)) == kPiece - 1 || rr == rend - 1) {
-#pragma unroll
-              for (int e = 0; e < NACC / 2; ++e) {
-                tacc[2 * e] = tp[e].x;
-                tacc[2 * e + 1] = tp[e].y;
-                tp[e] = make_float2(0.f, 0.f);
-              }
-              fold();
-            }
-          }
+        epi_sync();  // W of tile t complete
+        pend = t;
+        prow = 0;
+        pend_rows = min(MB, mi - MB * t);
+        u_ready = false;
+        // Spread over the next tile's first nch - 1 steps (all at once after
+        // the last tile).
+        prows = (t + 1 < ntiles && nch > 1) ? (pend_rows + nch - 2) / (nch - 1) : pend_rows;
+        if (t + 1 == ntiles) reduce_rows(pend_rows);
+      } else if (pend >= 0 && prow < pend_rows) {
+        reduce_rows(min(pend_rows, prow + prows));
+        if (prow == pend_rows && u_tile < t) {
+          epi_sync();  // every warp is done with S.u
+          if (et == 0 && ok) copy_u(u_issued++);  // U_i rows of tile t
+          u_tile = t;
         }
-        epi_sync();  // S.w and S.u are free again
-        if (et == 0 && ok && t + 1 < ntiles) copy_u(u_issued++);
       }
     }
     // A U copy still in flight must land before the CTA exits.
