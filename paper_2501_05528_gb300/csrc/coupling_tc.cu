@@ -6,11 +6,13 @@
 // points), splits it and the chunk's rows of V_j into three BF16 parts each and
 // accumulates the six significant part products in TMEM, small ones first, as
 // the mixed apply does (same error budget: ~2^-24 per operand, truncation only
-// at the size of one chunk's sum).  Each chunk's FP32 accumulator is added into
-// a Kahan-compensated copy of W in TMEM.  At the end of a row tile the
-// epilogue warps stage W and the tile's rows of U_i (FP32) in shared memory and
-// add U_i(tile)^T W into Kahan-compensated per-thread sums of Atilde_ij, 32
-// rows at a time.
+// at the size of one chunk's sum).  The generated tile goes straight into
+// tensor memory and is the MMA's A operand there, so the tensor core reads only
+// the V tile from shared memory.  Each chunk's FP32 accumulator is added into
+// a Kahan-compensated copy of W in TMEM.  After a row tile the epilogue warps
+// stage W and the tile's rows of U_i (FP32) in shared memory and add
+// U_i(tile)^T W into Kahan-compensated sums of Atilde_ij, spread over the
+// drain steps of the next tile.
 //
 // The points of every box are padded to a multiple of 64 in a box-padded order
 // (box j starts at poff[j]), so each chunk's V rows are one 64-point TMA tile
@@ -20,7 +22,7 @@
 //   warp 0      producer: V_j tiles (TMA) and chunk coordinates (bulk copies)
 //   warp 1      TMEM allocator and single-thread MMA issuer
 //   warps 2-5   epilogue: W sums in TMEM, then U_i^T W
-//   warps 6-13  generators: the 128 x 64 kernel tile in the swizzled layout
+//   warps 6-13  generators: the 128 x 64 kernel tile, written into TMEM
 // Every wait is bounded; a timeout is counted (tblr_device_timeouts), sets
 // the launch's status word and the CTA drains and exits.
 #include <algorithm>
@@ -42,18 +44,13 @@ constexpr int kParts = 3;  // BF16 parts per operand value
 constexpr int kGenWarps = 8;
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 32 * (2 + kEpiWarps + kGenWarps);
-constexpr int kTileBytes = MB * 128;  // one BF16 part of a kernel tile
 constexpr int kSmemLimit = 232448;    // 227 KiB of opt-in shared memory per CTA
 constexpr int kCS = 3;                // chunk coordinate slots (copied kCS - 1 ahead)
 constexpr int kQcBytes = KC / 2 * 12 * 4;
-constexpr int kPiece = 32;  // rows per compensated step of U^T W
 
 template <int KP>
 struct CplCfg {
   static constexpr int RS = KP + 4;  // row stride of W and U in shared memory (floats)
-  static constexpr int kStageBytes = kParts * (kTileBytes + KP * 128);
-  static constexpr int kFixed = 2048 + kCS * kQcBytes + MB * (RS + KP) * 4;
-  static constexpr int STAGES = (kSmemLimit - kFixed) / kStageBytes >= 3 ? 3 : 2;
   static constexpr int AC = KP >= 32 ? 4 : 2;     // Atilde columns per epilogue thread
   static constexpr int AA = KP * KP / (MB * AC);  // Atilde rows per epilogue thread
   static constexpr int NTC = KP / AC;             // epilogue threads across Atilde's columns
@@ -61,22 +58,25 @@ struct CplCfg {
   // Each epilogue thread's Atilde sums and compensations live in its own TMEM
   // lane when there are 16 or more of them (registers would spill).
   static constexpr bool kAccTmem = NACC >= 16;
-  // Two accumulator slots, W's running sum and its compensation (and the
-  // Atilde sums), rounded up to a power of two.
-  static constexpr uint32_t kTmemUsed = 4 * KP + (kAccTmem ? 2 * NACC : 0);
-  static constexpr uint32_t kTmemCols = kTmemUsed <= 64 ? 64 : kTmemUsed <= 128 ? 128
-                                        : kTmemUsed <= 256 ? 256 : 512;
+  // TMEM columns: two accumulator slots [0, 2 KP), W's sum and compensation
+  // [2 KP, 4 KP), the Atilde sums, then the kernel-tile stages from kABase:
+  // three BF16 parts of 32 columns each (64 points, two per 32-bit column).
+  static constexpr uint32_t kTmemCols = 512;
+  static constexpr uint32_t kAStage = kParts * (KC / 2);
+  static constexpr uint32_t kABase = (4 * KP + (kAccTmem ? 2 * NACC : 0) + 31) / 32 * 32;
+  static constexpr int STAGES = (kTmemCols - kABase) / kAStage >= 3 ? 3 : 2;
+  static constexpr int kStageBytes = kParts * KP * 128;  // the V_j tile
+  static constexpr int kFixed = 2048 + kCS * kQcBytes + MB * (RS + KP) * 4;
   static_assert(KP == 16 || KP == 32 || KP == 64, "rank tile");
+  static_assert(kABase + STAGES * kAStage <= kTmemCols, "tensor memory");
   static_assert(STAGES * kStageBytes + kFixed <= kSmemLimit, "shared memory");
   static_assert(AA * AC * MB == KP * KP, "Atilde tiling");
   static_assert(!kAccTmem || NACC % 16 == 0, "Atilde sums in TMEM groups of 16");
-  static_assert(kTmemUsed <= 512, "tensor memory");
 };
 
 template <int KP>
 struct __align__(1024) CplSmem {
   static constexpr int STAGES = CplCfg<KP>::STAGES, RS = CplCfg<KP>::RS;
-  uint8_t a[STAGES][kParts][kTileBytes];  // kernel tile h, m, l: 128 rows x 128 bytes
   uint8_t x[STAGES][kParts][KP * 128];    // V_j h, m, l: KP rows x 128 bytes
   float4 qc[kCS][3][4][8];                // chunk coordinates (the mixed apply's layout)
   float w[MB][RS];                        // W of the finished row tile
@@ -217,10 +217,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (use >= 1 && !pipe::wait_or_abort(S, a.status, &S.dempty[slot], (use - 1) & 1, timeouts))
           break;
         tc::tc_fence_after();
-        uint64_t ad[kParts], bd[kParts];
+        // A parts in TMEM (a K step of 16 BF16 is 8 columns), V parts in shared
+        // memory (a K step is 32 bytes: 2 in the descriptor's address field).
+        uint32_t at[kParts];
+        uint64_t bd[kParts];
 #pragma unroll
         for (int t = 0; t < kParts; ++t) {
-          ad[t] = tc::sw128_desc(tc::smem_u32(S.a[s][t]));
+          at[t] = tmem + C::kABase + s * C::kAStage + t * (KC / 2);
           bd[t] = tc::sw128_desc(tc::smem_u32(S.x[s][t]));
         }
         const uint32_t dt = tmem + slot * KP;
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int o = 0; o < 6; ++o) {
 #pragma unroll
           for (int kk = 0; kk < KC / 16; ++kk) {
-            tc::mma_f16(dt, ad[kOrder[o][0]] + 2 * kk, bd[kOrder[o][1]] + 2 * kk, idesc, acc);
+            tc::mma_f16_ts(dt, at[kOrder[o][0]] + 8 * kk, bd[kOrder[o][1]] + 2 * kk, idesc, acc);
             acc = 1u;
           }
         }
@@ -443,59 +446,60 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------------------------------------------------- generators
-    // Thread (jj, rbase): tile rows rbase + 32 ii (ii < 4) x points 8 jj ..
-    // 8 jj + 7 of each chunk, two points at a time in packed FP32x2 arithmetic.
-    const int gt = tid - 32 * (2 + kEpiWarps);  // 0 .. 255
-    const int jj = gt & 7;
-    const int rbase = gt >> 3;
+    // Generator warp gw writes TMEM lane quadrant q = warp % 4: its thread is
+    // tile row 32 q + lane and takes points 32 h .. 32 h + 31 of each chunk
+    // (h = gw / 4), two at a time in packed FP32x2 arithmetic; each group of
+    // four point pairs goes out as three 4-column TMEM stores (one per part).
+    const int gw = warp - (2 + kEpiWarps);  // 0 .. 7
+    const int q = warp & 3, h = gw >> 2;
+    const int r = 32 * q + lane;
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
     const float factor = entry_f32_factor<KERNEL>();
     const float2 f2 = make_float2(factor, factor);
-    float2 rx[4][3], lx[4][3];  // row coordinates, hi and lo, as (v, v) pairs
+    float2 rx[3], lx[3];  // this row's coordinates, hi and lo, as (v, v) pairs
     for (int st = 0; st < nsteps && !pipe::warp_aborted(S); ++st) {
       const int s = st % STAGES, cs = st % kCS, c = st % nch, t = st / nch;
       const uint32_t ph = (st / STAGES) & 1;
+      const int lr = MB * t + r;
       if (c == 0) {
-        // Coordinates of this thread's rows of tile t (zero past the box).
+        // Coordinates of this thread's row of tile t (zero past the box).
+        const int sp = pi + (lr < mi ? lr : 0);  // slot in the box-padded order
+        const int w = sp & (KC - 1), P = w >> 1, u = w & 1;
+        const float4 *blk = a.qst + (int64_t)(sp / KC) * (KC / 2 * 3) + (P & 3) * 8 + (P >> 2);
+        const float4 f0 = blk[0], f1 = blk[32], fz = blk[64];
+        const float v[6] = {u ? f0.y : f0.x, u ? f0.w : f0.z, u ? f1.y : f1.x,
+                            u ? f1.w : f1.z, u ? fz.y : fz.x, u ? fz.w : fz.z};
 #pragma unroll
-        for (int ii = 0; ii < 4; ++ii) {
-          const int lr = MB * t + rbase + 32 * ii;
-          const int sp = pi + (lr < mi ? lr : 0);  // slot in the box-padded order
-          const int w = sp & (KC - 1), P = w >> 1, u = w & 1;
-          const float4 *blk = a.qst + (int64_t)(sp / KC) * (KC / 2 * 3) + (P & 3) * 8 + (P >> 2);
-          const float4 f0 = blk[0], f1 = blk[32], fz = blk[64];
-          const float v[6] = {u ? f0.y : f0.x, u ? f0.w : f0.z, u ? f1.y : f1.x,
-                              u ? f1.w : f1.z, u ? fz.y : fz.x, u ? fz.w : fz.z};
-#pragma unroll
-          for (int ax = 0; ax < 3; ++ax) {
-            rx[ii][ax] = make_float2(-v[ax], -v[ax]);
-            lx[ii][ax] = make_float2(-v[3 + ax], -v[3 + ax]);
-          }
+        for (int ax = 0; ax < 3; ++ax) {
+          rx[ax] = make_float2(-v[ax], -v[ax]);
+          lx[ax] = make_float2(-v[3 + ax], -v[3 + ax]);
         }
       }
       if (st >= STAGES && !pipe::warp_wait(S, a.status, &S.empty[s], ph ^ 1, timeouts)) break;
       if (!pipe::warp_wait(S, a.status, &S.cfull[cs], (st / kCS) & 1, timeouts)) break;
+      tc::tc_fence_after();  // the MMAs that read this TMEM stage have completed
       const int r0 = MB * t, q0 = KC * c;
       // A chunk away from the diagonal and the ragged edges needs no per-entry
       // checks (the test is uniform over the CTA).
       const bool clean =
           r0 + MB <= mi && q0 + KC <= mj && (i != j || q0 + KC <= r0 || q0 >= r0 + MB);
+      const uint32_t a_t = tmem + lanes + C::kABase + s * C::kAStage + 16 * h;
 #pragma unroll
-      for (int ii = 0; ii < 4; ++ii) {
-        const int r = rbase + 32 * ii, lr = r0 + r;
+      for (int g = 0; g < 4; ++g) {
         uint32_t pw[kParts][4];
 #pragma unroll
         for (int pr = 0; pr < 4; ++pr) {
-          const int P = 4 * jj + pr;  // point pair within the chunk
+          const int jj = 4 * h + g;   // point pair P = 4 jj + pr = 16 h + 4 g + pr
           const float4 q0v = S.qc[cs][0][pr][jj], q1v = S.qc[cs][1][pr][jj],
                        q2v = S.qc[cs][2][pr][jj];
-          const float2 dx = __fadd2_rn(__fadd2_rn(rx[ii][0], make_float2(q0v.x, q0v.y)),
-                                       __fadd2_rn(lx[ii][0], make_float2(q1v.z, q1v.w)));
-          const float2 dy = __fadd2_rn(__fadd2_rn(rx[ii][1], make_float2(q0v.z, q0v.w)),
-                                       __fadd2_rn(lx[ii][1], make_float2(q2v.x, q2v.y)));
+          const float2 dx = __fadd2_rn(__fadd2_rn(rx[0], make_float2(q0v.x, q0v.y)),
+                                       __fadd2_rn(lx[0], make_float2(q1v.z, q1v.w)));
+          const float2 dy = __fadd2_rn(__fadd2_rn(rx[1], make_float2(q0v.z, q0v.w)),
+                                       __fadd2_rn(lx[1], make_float2(q2v.x, q2v.y)));
           float2 r2;
           if (KERNEL == TBLR_KERNEL_LAPLACE3D) {
-            const float2 dz = __fadd2_rn(__fadd2_rn(rx[ii][2], make_float2(q1v.x, q1v.y)),
-                                         __fadd2_rn(lx[ii][2], make_float2(q2v.z, q2v.w)));
+            const float2 dz = __fadd2_rn(__fadd2_rn(rx[2], make_float2(q1v.x, q1v.y)),
+                                         __fadd2_rn(lx[2], make_float2(q2v.z, q2v.w)));
             r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
           } else {
             r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
@@ -503,19 +507,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           float2 v = __fmul2_rn(
               make_float2(entry_f32_of_r2<KERNEL>(r2.x), entry_f32_of_r2<KERNEL>(r2.y)), f2);
           if (!clean) {
-            const int lq = q0 + 2 * P;
+            const int lq = q0 + 2 * (4 * jj + pr);
             if (lr >= mi || lq >= mj || (i == j && lq == lr)) v.x = 0.f;
             if (lr >= mi || lq + 1 >= mj || (i == j && lq + 1 == lr)) v.y = 0.f;
           }
           pipe::split3(v.x, v.y, pw[0][pr], pw[1][pr], pw[2][pr]);
         }
-        const int off = r * 128 + ((jj ^ (r & 7)) << 4);  // 128-byte swizzle
 #pragma unroll
         for (int p = 0; p < kParts; ++p)
-          *reinterpret_cast<uint4 *>(S.a[s][p] + off) =
-              make_uint4(pw[p][0], pw[p][1], pw[p][2], pw[p][3]);
+          tc::tmem_st4(a_t + p * (KC / 2) + 4 * g, pw[p][0], pw[p][1], pw[p][2], pw[p][3]);
       }
-      tc::fence_proxy_async_smem();
+      tc::tmem_wait_st();
+      tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) {
         tc::mbar_arrive(&S.cfree[cs]);
