@@ -275,8 +275,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int g = 0; g < NACC / 16; ++g) {
           float hv[16], cv[16];
           tc::tmem_ld16x2(acc_t + 16 * g, acc_t + NACC + 16 * g, hv, cv);
+          float tv[16];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) kahan_add(hv[e], cv[e], tacc[16 * g + e]);
+          for (int e = 0; e < 16; ++e) tv[e] = tacc[16 * g + e];
+          kahan_add16(hv, cv, tv);
           tc::tmem_st16(acc_t + 16 * g, hv);
           tc::tmem_st16(acc_t + NACC + 16 * g, cv);
         }
@@ -378,13 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int e = 0; e < 16; ++e) hv[e] = cv[e] = 0.f;
           }
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {  // Kahan: hi + (d - c), c keeps the lost low part
-            const float yv = dv[e] - cv[e];
-            const float tt = hv[e] + yv;
-            cv[e] = (tt - hv[e]) - yv;
-            hv[e] = tt;
-          }
+          kahan_add16(hv, cv, dv);  // hi + (d - c); c keeps the lost low part
           if (last) {
             float4 *wr = reinterpret_cast<float4 *>(&S.w[r][cg * 16]);
 #pragma unroll

@@ -81,4 +81,21 @@ __device__ __forceinline__ void kahan_add(float &hi, float &c, float v) {
   hi = t;
 }
 
+// The same on 2 x 16 values in packed FP32x2 arithmetic (a - b is the exactly
+// rounded fma(b, -1, a)), so every result is bitwise the scalar one.
+__device__ __forceinline__ void kahan_add16(float (&hi)[16], float (&c)[16], const float (&v)[16]) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+  for (int e = 0; e < 16; e += 2) {
+    const float2 h2 = make_float2(hi[e], hi[e + 1]), c2 = make_float2(c[e], c[e + 1]);
+    const float2 y = __ffma2_rn(c2, m1, make_float2(v[e], v[e + 1]));  // v - c
+    const float2 t = __fadd2_rn(h2, y);                                 // hi + y
+    const float2 cn = __ffma2_rn(y, m1, __ffma2_rn(h2, m1, t));         // (t - hi) - y
+    hi[e] = t.x;
+    hi[e + 1] = t.y;
+    c[e] = cn.x;
+    c[e + 1] = cn.y;
+  }
+}
+
 }  // namespace tblr

@@ -310,13 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int cg = 0; cg < UC / 16; ++cg) {
           const uint32_t col = h * UC + cg * 16;
           tc::tmem_ld16x3(d_t + cg * 16, hi_t + col, cc_t + col, dv, hv, cv);
-#pragma unroll
-          for (int t = 0; t < 16; ++t) {  // Kahan: hi + (d - c), c keeps the lost low part
-            const float yv = dv[t] - cv[t];
-            const float tt = hv[t] + yv;
-            cv[t] = (tt - hv[t]) - yv;
-            hv[t] = tt;
-          }
+          kahan_add16(hv, cv, dv);  // hi + (d - c); c keeps the lost low part
           tc::tmem_st16(hi_t + col, hv);
           tc::tmem_st16(cc_t + col, cv);
         }
