@@ -140,4 +140,38 @@ __device__ __forceinline__ double warp_min(double v) {
   return v;
 }
 
+// The boxes whose columns enter B_ij (§6.1): every box of colour(j) for the
+// paper's identity probe, or j alone for the exact discrepancy block.  The
+// whole block scans the colours (a ballot per warp, then the warps' counts in
+// order), writes the set in ascending box order to shared memory and returns
+// its size.  Every thread of the block must call it (blockDim.x a multiple of 32).
+__device__ __forceinline__ int block_probe_set(int j, int mode, const int32_t *__restrict__ colour,
+                                               int b, int *set) {
+  __shared__ int wcount[32];
+  if (mode == TBLR_NEARFIELD_EXACT) {
+    if (threadIdx.x == 0) set[0] = j;
+    __syncthreads();
+    return 1;
+  }
+  const int g = colour[j];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int base = 0;
+  for (int x0 = 0; x0 < b; x0 += blockDim.x) {
+    const int x = x0 + threadIdx.x;
+    const bool hit = x < b && colour[x] == g;
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) wcount[w] = __popc(m);
+    __syncthreads();
+    int off = base, tot = 0;
+    for (int v = 0; v < nw; ++v) {
+      if (v < w) off += wcount[v];
+      tot += wcount[v];
+    }
+    if (hit) set[off + __popc(m & ((1u << lane) - 1u))] = x;
+    base += tot;
+    __syncthreads();
+  }
+  return base;
+}
+
 }  // namespace tblr

@@ -102,27 +102,6 @@ __global__ void __launch_bounds__(kThreads) coupling_kernel(Op op, const int32_t
   }
 }
 
-// The boxes whose columns enter B_ij: every box of colour(j) for the paper's
-// identity probe, or j alone for the exact discrepancy block.  Written to
-// shared memory; returns the count.
-__device__ int probe_set(int j, int mode, const int32_t *__restrict__ colour, int b, int *set) {
-  __shared__ int cnt;
-  if (mode == TBLR_NEARFIELD_EXACT) {
-    if (threadIdx.x == 0) set[0] = j;
-    __syncthreads();
-    return 1;
-  }
-  if (threadIdx.x == 0) {
-    const int g = colour[j];
-    int c = 0;
-    for (int x = 0; x < b; ++x)
-      if (colour[x] == g) set[c++] = x;
-    cnt = c;
-  }
-  __syncthreads();
-  return cnt;
-}
-
 // M_is = sum_{c in set} Atilde_ic V_c(0:m_j, :)^T  (k x m_j; rows of V_c
 // beyond m_c count as zero).  M[((i*S3 + s)*k + a)*mmax + q].
 __global__ void __launch_bounds__(kThreads) nf_lowrank_kernel(
@@ -135,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) nf_lowrank_kernel(
   if (s >= nnbr[i]) return;
   const int j = nbr[(int64_t)i * s3 + s];
   const int mj = offsets[j + 1] - offsets[j];
-  const int ns = probe_set(j, mode, colour, b, set);
+  const int ns = block_probe_set(j, mode, colour, b, set);
   double *out = M + ((int64_t)i * s3 + s) * k * mmax;
   for (int idx = threadIdx.x; idx < k * mj; idx += kThreads) {
     const int a = idx / mj, q = idx % mj;
@@ -165,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) nf_block_kernel(
   const int j = nbr[(int64_t)i * s3 + s];
   const int oi = offsets[i], mi = offsets[i + 1] - oi;
   const int mj = offsets[j + 1] - offsets[j];
-  const int ns = probe_set(j, mode, colour, b, set);
+  const int ns = block_probe_set(j, mode, colour, b, set);
   const double *Mi = M + ((int64_t)i * s3 + s) * k * mmax;
   double *out = Bn + nf_off[(int64_t)i * s3 + s];
   for (int idx = threadIdx.x; idx < mi * mj; idx += kThreads) {

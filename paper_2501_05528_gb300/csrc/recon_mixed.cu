@@ -256,25 +256,6 @@ __global__ void __launch_bounds__(kThreads, 2) coupling_f32_kernel(
     }
 }
 
-// The boxes whose columns enter B_ij (every box of colour(j) for the probe
-// reading, j alone for the exact one), in shared memory.
-__device__ int probe_set_f(int j, int mode, const int32_t *__restrict__ colour, int b, int *set) {
-  __shared__ int cnt;
-  if (threadIdx.x == 0) {
-    int c = 0;
-    if (mode == TBLR_NEARFIELD_EXACT) {
-      set[c++] = j;
-    } else {
-      const int g = colour[j];
-      for (int x = 0; x < b; ++x)
-        if (colour[x] == g) set[c++] = x;
-    }
-    cnt = c;
-  }
-  __syncthreads();
-  return cnt;
-}
-
 // CTA per (i, s, 128-column tile of M): M_is(a, q) for a < k, q in the tile.
 // Each set member c contributes Atilde_ic V_c(q, :)^T: Atilde_ic^T and the
 // tile's columns of V_c^T are staged in shared memory (t-major, so a thread
@@ -298,7 +279,7 @@ __global__ void __launch_bounds__(kThreads) nf_lowrank_f32_kernel(
   float *As = sf;               // [64][kAS]: As[t * kAS + a] = Atilde_ic(a, t)
   float *Vs = As + 64 * kAS;    // [64][kVS]: Vs[t * kVS + q] = V_c(q0 + q, t)
   int *set = reinterpret_cast<int *>(Vs + 64 * kVS);
-  const int ns = probe_set_f(j, mode, colour, b, set);
+  const int ns = block_probe_set(j, mode, colour, b, set);
   for (int idx = tid; idx < 64 * kAS; idx += kThreads) As[idx] = 0.f;  // rows a >= k stay 0
   const int ta = tid % 16, tq = tid / 16;  // rows 4 ta + x, columns 8 tq + y
   float hi[4][8], cc[4][8];
@@ -375,6 +356,7 @@ __global__ void transpose_v_f32(const double *__restrict__ v, int64_t n, int k,
 // column coordinates of each probe box are staged once per tile, the tile's
 // rows of U_i and columns of M_is sit in shared memory for the low-rank part.
 constexpr int kBT = 64;
+constexpr int kNSC = 32;  // probe-set boxes whose coordinates are staged per barrier
 template <int KERNEL>
 __global__ void __launch_bounds__(kThreads) nf_block_f32_kernel(
     const float *__restrict__ chp, const float *__restrict__ clp, int64_t npad,
@@ -393,10 +375,10 @@ __global__ void __launch_bounds__(kThreads) nf_block_f32_kernel(
   if (p0 >= mi) return;
   float *Us = sf;                          // [kBT][k + 1]
   float *Ms = Us + kBT * (k + 1);          // [k][kBT + 4]
-  float *qh = Ms + k * (kBT + 4);          // [3][kBT]
-  float *ql = qh + 3 * kBT;                // [3][kBT]
-  int *set = reinterpret_cast<int *>(ql + 3 * kBT);
-  const int ns = probe_set_f(j, mode, colour, b, set);
+  float *qh = Ms + k * (kBT + 4);          // [kNSC][3][kBT]
+  float *ql = qh + kNSC * 3 * kBT;         // [kNSC][3][kBT]
+  int *set = reinterpret_cast<int *>(ql + kNSC * 3 * kBT);
+  const int ns = block_probe_set(j, mode, colour, b, set);
   for (int idx = tid; idx < kBT * k; idx += kThreads) {
     const int r = idx / k, a = idx % k;
     Us[r * (k + 1) + a] = (p0 + r < mi) ? (float)U[((int64_t)oi + p0 + r) * k + a] : 0.f;
@@ -407,74 +389,114 @@ __global__ void __launch_bounds__(kThreads) nf_block_f32_kernel(
     Ms[a * (kBT + 4) + q] = (q0 + q < mj) ? Mi[(int64_t)a * mmax + q0 + q] : 0.f;
   }
   const int tx = tid % 16, ty = tid / 16;   // rows p0 + 4 ty + x, columns q0 + 4 tx + y
-  float rh[4][3], rl[4][3];
+  // Row coordinates as (v, v) pairs; the step's point coordinates are staged
+  // negated, so a column pair (q, q + 1) is one 8-byte load and every
+  // difference, square and compensated add below is packed FP32x2.
+  float2 rh[4][3], rl[4][3];
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
     const int64_t gp = (int64_t)oi + p0 + 4 * ty + x;
     const bool in = p0 + 4 * ty + x < mi;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-      rh[x][ax] = in ? chp[ax * npad + gp] : 0.f;
-      rl[x][ax] = in ? clp[ax * npad + gp] : 0.f;
+      const float h = in ? chp[ax * npad + gp] : 0.f, l = in ? clp[ax * npad + gp] : 0.f;
+      rh[x][ax] = make_float2(h, h);
+      rl[x][ax] = make_float2(l, l);
     }
   }
-  float hi[4][4], cc[4][4];
+  const float2 f2 = make_float2(entry_f32_factor<KERNEL>(), entry_f32_factor<KERNEL>());
+  const float2 m1 = make_float2(-1.f, -1.f);
+  float2 hi[4][2], cc[4][2];  // columns (4 tx + 2 yp, 4 tx + 2 yp + 1)
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) hi[x][y] = cc[x][y] = 0.f;
-  for (int u = 0; u < ns; ++u) {
-    const int c = set[u];
-    const int oc = offsets[c], mc = offsets[c + 1] - oc;
-    if (q0 >= mc) continue;  // uniform over the CTA
+    for (int yp = 0; yp < 2; ++yp) hi[x][yp] = cc[x][yp] = make_float2(0.f, 0.f);
+  // hi + v with compensation c (packed Kahan; a - b as the exactly rounded fma(b, -1, a)).
+  auto kahan2 = [&](float2 &h, float2 &c, float2 v) {
+    const float2 y = __ffma2_rn(c, m1, v);
+    const float2 t = __fadd2_rn(h, y);
+    c = __ffma2_rn(y, m1, __ffma2_rn(h, m1, t));
+    h = t;
+  };
+  for (int u0 = 0; u0 < ns; u0 += kNSC) {
+    // The step's columns of up to kNSC probe-set boxes, staged at once.
+    const int nb = min(kNSC, ns - u0);
     __syncthreads();
-    for (int idx = tid; idx < 3 * kBT; idx += kThreads) {
-      const int ax = idx / kBT, q = idx % kBT;
-      const bool in = q0 + q < mc;
-      qh[idx] = in ? chp[ax * npad + oc + q0 + q] : 0.f;
-      ql[idx] = in ? clp[ax * npad + oc + q0 + q] : 0.f;
+    for (int idx = tid; idx < nb * 3 * kBT; idx += kThreads) {
+      const int uu = idx / (3 * kBT), ax = (idx / kBT) % 3, q = idx % kBT;
+      const int cb = set[u0 + uu];
+      const int ocb = offsets[cb], mcb = offsets[cb + 1] - ocb;
+      const bool in = q0 + q < mcb;
+      qh[idx] = in ? -chp[ax * npad + ocb + q0 + q] : 0.f;
+      ql[idx] = in ? -clp[ax * npad + ocb + q0 + q] : 0.f;
     }
     __syncthreads();
+    for (int uu = 0; uu < nb; ++uu) {
+      const int c = set[u0 + uu];
+      const int mc = offsets[c + 1] - offsets[c];
+      if (q0 >= mc) continue;  // uniform over the CTA
+      const float *qhb = qh + uu * 3 * kBT, *qlb = ql + uu * 3 * kBT;
+      // A tile inside both boxes and off the diagonal needs no per-entry checks.
+      const bool clean = q0 + kBT <= mc && q0 + kBT <= mj && p0 + kBT <= mi && c != i;
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int q = 4 * tx + y;
-      const float ch[3] = {qh[q], qh[kBT + q], qh[2 * kBT + q]};
-      const float cl[3] = {ql[q], ql[kBT + q], ql[2 * kBT + q]};
-      const bool qin = q0 + q < mc && q0 + q < mj;
+      for (int yp = 0; yp < 2; ++yp) {
+        const int q = 4 * tx + 2 * yp;
+        float2 nh[3], nl[3];
 #pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        float v = entry_f32<KERNEL>(rh[x], rl[x], ch, cl);
-        const bool diag = (c == i) && (p0 + 4 * ty + x == q0 + q);
-        if (!qin || diag || p0 + 4 * ty + x >= mi) v = 0.f;
-        kahan_add(hi[x][y], cc[x][y], v);
+        for (int ax = 0; ax < 3; ++ax) {
+          nh[ax] = *reinterpret_cast<const float2 *>(&qhb[ax * kBT + q]);
+          nl[ax] = *reinterpret_cast<const float2 *>(&qlb[ax * kBT + q]);
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const float2 dx = __fadd2_rn(__fadd2_rn(rh[x][0], nh[0]), __fadd2_rn(rl[x][0], nl[0]));
+          const float2 dy = __fadd2_rn(__fadd2_rn(rh[x][1], nh[1]), __fadd2_rn(rl[x][1], nl[1]));
+          float2 r2;
+          if (KERNEL == TBLR_KERNEL_LAPLACE3D) {
+            const float2 dz = __fadd2_rn(__fadd2_rn(rh[x][2], nh[2]), __fadd2_rn(rl[x][2], nl[2]));
+            r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+          } else {
+            r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+          }
+          float2 v = __fmul2_rn(
+              make_float2(entry_f32_of_r2<KERNEL>(r2.x), entry_f32_of_r2<KERNEL>(r2.y)), f2);
+          if (!clean) {
+            const int p = p0 + 4 * ty + x, qq = q0 + q;
+            if (qq >= mc || qq >= mj || p >= mi || (c == i && p == qq)) v.x = 0.f;
+            if (qq + 1 >= mc || qq + 1 >= mj || p >= mi || (c == i && p == qq + 1)) v.y = 0.f;
+          }
+          kahan2(hi[x][yp], cc[x][yp], v);
+        }
       }
     }
   }
   __syncthreads();
-  // Low-rank part U_i M_is, subtracted from the Kahan sums 8 rank terms at a
-  // time (so each FP32 partial sum has at most 8 roundings).
+  // Low-rank part U_i M_is, subtracted from the compensated sums 8 rank terms
+  // at a time (so each FP32 partial sum has at most 8 roundings).
   for (int a0 = 0; a0 < k; a0 += 8) {
-    float lr[4][4];
+    float2 lr[4][2];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) lr[x][y] = 0.f;
+      for (int yp = 0; yp < 2; ++yp) lr[x][yp] = make_float2(0.f, 0.f);
     const int a1 = min(a0 + 8, k);
     for (int a = a0; a < a1; ++a) {
-      float uu[4], mm[4];
+      float uu[4];
 #pragma unroll
       for (int x = 0; x < 4; ++x) uu[x] = Us[(4 * ty + x) * (k + 1) + a];
-#pragma unroll
-      for (int y = 0; y < 4; ++y) mm[y] = Ms[a * (kBT + 4) + 4 * tx + y];
+      const float4 m4 = *reinterpret_cast<const float4 *>(&Ms[a * (kBT + 4) + 4 * tx]);
+      const float2 mm[2] = {make_float2(m4.x, m4.y), make_float2(m4.z, m4.w)};
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) lr[x][y] = fmaf(uu[x], mm[y], lr[x][y]);
+        for (int yp = 0; yp < 2; ++yp)
+          lr[x][yp] = __ffma2_rn(make_float2(uu[x], uu[x]), mm[yp], lr[x][yp]);
     }
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) kahan_add(hi[x][y], cc[x][y], -lr[x][y]);
+      for (int yp = 0; yp < 2; ++yp)
+        kahan2(hi[x][yp], cc[x][yp], make_float2(-lr[x][yp].x, -lr[x][yp].y));
   }
   double *out = Bn + nf_off[(int64_t)i * s3 + s];
 #pragma unroll
@@ -484,7 +506,9 @@ __global__ void __launch_bounds__(kThreads) nf_block_f32_kernel(
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
       const int q = q0 + 4 * tx + y;
-      if (q < mj) out[(int64_t)p * mj + q] = (double)hi[x][y] - (double)cc[x][y];
+      const float h = y & 1 ? hi[x][y >> 1].y : hi[x][y >> 1].x;
+      const float c = y & 1 ? cc[x][y >> 1].y : cc[x][y >> 1].x;
+      if (q < mj) out[(int64_t)p * mj + q] = (double)h - (double)c;
     }
   }
 }
@@ -624,7 +648,7 @@ int nearfield_mixed(const Prob &P, const tblr_layout *lay, const double *u, cons
                           smem_lr, s>>>(lay->offsets, lay->nbr, lay->nnbr, lay->colour, (int)P.b,
                                         P.s3, P.k, mmax, P.nearfield, at, vt, P.n, M);
   TBLR_TRY(launch_status("nf_lowrank_f32_kernel"));
-  const size_t smem_b = sizeof(float) * (kBT * (P.k + 1) + P.k * (kBT + 4) + 6 * kBT) +
+  const size_t smem_b = sizeof(float) * (kBT * (P.k + 1) + P.k * (kBT + 4) + kNSC * 6 * kBT) +
                         sizeof(int) * P.b;
   TBLR_REQUIRE(smem_b <= 220 * 1024, "mixed near field: too many boxes for the probe set");
   const int tiles = (int)cdiv(mmax, kBT);
