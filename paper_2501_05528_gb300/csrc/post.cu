@@ -414,7 +414,7 @@ __global__ void combine_kernel(const double *__restrict__ yz, const double *__re
 }
 
 // ------------------------------------------------------------------- a6 col
-constexpr int kColThreads = 256;
+constexpr int kColThreads = 512;
 constexpr int kRMax = 112;
 
 __device__ double block_sum(double v, double *red) {
@@ -529,8 +529,8 @@ __global__ void __launch_bounds__(kColThreads) col_kernel(ColArgs A) {
   double *W = A.W + (int64_t)off * r;
   double *E = A.E + (int64_t)off * k;
   double *tauh = sm;             // [kRMax]
-  double *red = tauh + kRMax;    // [8]
-  double *B = red + 8;           // [q][r]: column a of R^T (= row a of R)
+  double *red = tauh + kRMax;    // [kColThreads / 32]
+  double *B = red + kColThreads / 32;  // [q][r]: column a of R^T (= row a of R)
   double *X = B + q * r;         // [q][q]: column-major rotations
   double *sig = X + q * q;       // [q]
   int *order = reinterpret_cast<int *>(sig + q);  // [q]
@@ -715,7 +715,8 @@ __global__ void __launch_bounds__(kColThreads) col_kernel(ColArgs A) {
 
 size_t col_smem(int r) {
   const int q = r;  // q <= r
-  return sizeof(double) * (kRMax + 8 + (size_t)q * r + (size_t)q * q + q) + sizeof(int) * q;
+  return sizeof(double) * (kRMax + kColThreads / 32 + (size_t)q * r + (size_t)q * q + q) +
+         sizeof(int) * q;
 }
 
 }  // namespace
