@@ -24,9 +24,10 @@
  *   detected on the host before anything is enqueued; CUDA errors are reported
  *   as TBLR_ECUDA.  tblr_last_error() gives a message for the calling thread.
  * - Floating point: FP64 unless the problem selects TBLR_MIXED.  Then the
- *   sketch contraction (tblr_sketch, tblr_apply) runs on the tensor cores in
- *   split FP16 with FP32 accumulation, coupling and near field run on the FP32
- *   pipes with compensated sums, and tag decode, combine and col stay FP64.
+ *   sketch contraction (tblr_sketch, tblr_apply, tblr_tagged_sketch) and the
+ *   coupling's A_ij V_j run on the tensor cores as three-part BF16 products
+ *   with FP32 accumulation, U_i^T W and the near field run on the FP32 pipes
+ *   with compensated sums, and tag decode, combine and col stay FP64.
  *
  * Symbols used below: d dimension (1..3); n points; b boxes (product of grid);
  * ell = 3^d + 1 + e tag columns; r = k + p; C = ell * r sketch columns per side;
@@ -57,7 +58,7 @@ extern "C" {
 
 /* Precision mode (see "Floating point" above). */
 #define TBLR_FP64  0
-#define TBLR_MIXED 1  /* three-part BF16 tensor-core sketch; FP32 coupling and near field */
+#define TBLR_MIXED 1  /* three-part BF16 tensor-core sketch and coupling; FP32 near field */
 
 /* Near-field reading (§6.1): the paper's identity probe, or the exact block. */
 #define TBLR_NEARFIELD_PROBE 0  /* B_ij = sum_{c: colour(c)=colour(j)} (A_ic - U_i At_ic V_c^T)(:, 0:m_j) */
@@ -258,12 +259,18 @@ int tblr_col(const tblr_problem *prob, const tblr_layout *lay, const double *s,
  * Atilde_ij = U_i^T A_ij V_j for ALL box pairs: at[((i*b + j)*k + a)*k + c],
  * zero outside a < k_i, c < k_j.  u, v: [n*k]; ranks: [b]; m_max = max_i m_i
  * (as returned by tblr_nearfield_offsets).  FP64, or with TBLR_MIXED on the
- * FP32 pipes (double-float coordinates, chunked and compensated sums, ~1e-7
- * relative).  With TBLR_SKETCH_SELFADJOINT the caller passes v = u (A = A^T)
- * and only i <= j are formed, Atilde_ji = Atilde_ij^T.
- * ws: tblr_coupling_workspace bytes (0 for FP64; with TBLR_MIXED the FP32
- * copies of U, V and the double-float coordinates), 256-byte aligned.
- * Limits: k <= 64; mixed: m_max <= ~780. */
+ * tensor cores: A_ij V_j as three-part BF16 products with FP32 accumulation
+ * per 64-point chunk and compensated sums, then U_i^T W in FP32 with
+ * compensated sums (~1e-7 relative; the environment variable
+ * TBLR_COUPLING_SIMT=1 selects an FP32 SIMT form of the same sums).  With
+ * TBLR_SKETCH_SELFADJOINT the caller passes v = u (A = A^T) and only i <= j
+ * are formed, Atilde_ji = Atilde_ij^T.
+ * ws: tblr_coupling_workspace bytes (0 for FP64; with TBLR_MIXED the points
+ * and U in a per-box padded order, the BF16 parts of V and a status word),
+ * 256-byte aligned.  A device-side wait that times out makes the output
+ * undefined and is counted by tblr_device_timeouts.
+ * Limits: k <= 64; mixed: b <= 65535 and n < 2^30 (the SIMT form also
+ * m_max <= ~780). */
 size_t tblr_coupling_workspace(const tblr_problem *prob);
 int tblr_coupling(const tblr_problem *prob, const tblr_layout *lay, const double *dense,
                   const double *u, const double *v, const int32_t *ranks, int32_t m_max,
