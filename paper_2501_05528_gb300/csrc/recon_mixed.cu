@@ -282,11 +282,14 @@ __global__ void __launch_bounds__(kThreads) nf_lowrank_f32_kernel(
   const int ns = block_probe_set(j, mode, colour, b, set);
   for (int idx = tid; idx < 64 * kAS; idx += kThreads) As[idx] = 0.f;  // rows a >= k stay 0
   const int ta = tid % 16, tq = tid / 16;  // rows 4 ta + x, columns 8 tq + y
-  float hi[4][8], cc[4][8];
+  // Column pairs (8 tq + 2 yp, 8 tq + 2 yp + 1) in packed FP32x2; the
+  // compensated adds use a - b = fma(b, -1, a) (exactly rounded).
+  const float2 m1 = make_float2(-1.f, -1.f);
+  float2 hi[4][4], cc[4][4];
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
-    for (int y = 0; y < 8; ++y) hi[x][y] = cc[x][y] = 0.f;
+    for (int yp = 0; yp < 4; ++yp) hi[x][yp] = cc[x][yp] = make_float2(0.f, 0.f);
   for (int u = 0; u < ns; ++u) {
     const int c = set[u];
     const int oc = offsets[c], mc = offsets[c + 1] - oc;
@@ -304,27 +307,34 @@ __global__ void __launch_bounds__(kThreads) nf_lowrank_f32_kernel(
     }
     __syncthreads();
     for (int t0 = 0; t0 < k; t0 += 16) {
-      float acc[4][8];
+      float2 acc[4][4];
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+        for (int yp = 0; yp < 4; ++yp) acc[x][yp] = make_float2(0.f, 0.f);
       const int t1 = min(t0 + 16, k);
       for (int t = t0; t < t1; ++t) {
         const float4 av = *reinterpret_cast<const float4 *>(As + t * kAS + 4 * ta);
         const float4 v0 = *reinterpret_cast<const float4 *>(Vs + t * kVS + 8 * tq);
         const float4 v1 = *reinterpret_cast<const float4 *>(Vs + t * kVS + 8 * tq + 4);
         const float ar[4] = {av.x, av.y, av.z, av.w};
-        const float vr[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        const float2 vp[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w),
+                              make_float2(v1.x, v1.y), make_float2(v1.z, v1.w)};
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(ar[x], vr[y], acc[x][y]);
+          for (int yp = 0; yp < 4; ++yp)
+            acc[x][yp] = __ffma2_rn(make_float2(ar[x], ar[x]), vp[yp], acc[x][yp]);
       }
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 8; ++y) kahan_add(hi[x][y], cc[x][y], acc[x][y]);
+        for (int yp = 0; yp < 4; ++yp) {
+          const float2 y = __ffma2_rn(cc[x][yp], m1, acc[x][yp]);
+          const float2 tt = __fadd2_rn(hi[x][yp], y);
+          cc[x][yp] = __ffma2_rn(y, m1, __ffma2_rn(hi[x][yp], m1, tt));
+          hi[x][yp] = tt;
+        }
     }
   }
   float *out = M + ((int64_t)i * s3 + s) * k * mmax;
@@ -335,7 +345,9 @@ __global__ void __launch_bounds__(kThreads) nf_lowrank_f32_kernel(
 #pragma unroll
     for (int y = 0; y < 8; ++y) {
       const int q = q0 + 8 * tq + y;
-      if (q < mj) out[(int64_t)a * mmax + q] = hi[x][y] - cc[x][y];
+      const float h = y & 1 ? hi[x][y >> 1].y : hi[x][y >> 1].x;
+      const float c = y & 1 ? cc[x][y >> 1].y : cc[x][y >> 1].x;
+      if (q < mj) out[(int64_t)a * mmax + q] = h - c;
     }
   }
 }

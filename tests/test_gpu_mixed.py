@@ -128,10 +128,10 @@ def test_mixed_tagged_sketch_every_tile_width(kind, d, grid, n, k):
         assert row_err.max() < MIXED_BOUND
 
 
-# Coupling blocks on the tensor cores: boxes of 130 to 400 points (several
+# Coupling blocks on the tensor cores: boxes of 130 to 800 points (several
 # 128-row tiles and 64-point chunks, ragged tails), every rank tile (k -> 16,
-# 32, 64 columns), ranks below k and zero, empty boxes, and the self-adjoint
-# mirror.  Columns of U and V past a box's rank hold garbage that must be ignored.
+# 32, 64 columns, k = 1), ranks below k and zero, empty boxes, and the
+# self-adjoint mirror.  Columns of U and V past a box's rank hold garbage that must be ignored.
 @pytest.mark.parametrize("kind,d,grid,n,k,hi,selfadjoint", [
     ("laplace2d", 2, (3, 3), 3001, 6, 1.0, False),
     ("laplace3d", 3, (2, 2, 2), 2100, 20, 1.0, False),
@@ -139,6 +139,8 @@ def test_mixed_tagged_sketch_every_tile_width(kind, d, grid, n, k):
     ("laplace3d", 3, (2, 2, 2), 1500, 64, 1.0, False),
     ("laplace2d", 2, (3, 3), 3001, 32, 1.0, True),
     ("laplace3d", 3, (2, 2, 2), 2100, 64, 1.0, True),
+    ("laplace2d", 2, (2, 2), 3000, 1, 1.0, False),          # ~750-point boxes: 6 row tiles
+    ("laplace3d", 3, (2, 2, 1), 2800, 40, 1.0, True),
 ])
 def test_mixed_coupling_matches_dense_definition(kind, d, grid, n, k, hi, selfadjoint):
     """Atilde_ij = U_i(:, :k_i)^T A(I_i, I_j) V_j(:, :k_j) (§2.5), zero past the ranks."""
