@@ -89,6 +89,17 @@ def make_inputs(w, rank=0):
     return pts, T, G, H
 
 
+
+def launches_per_compression(mixed, tagged, selfadjoint=False):
+    """Kernel launches of the library for one compression: tessellate 4, near-field offsets 2,
+    col 2 (1 self-adjoint), coupling 1, near field 2, decode 1; mixed precision adds the
+    coupling's 4 operand passes (box-padded offsets, staged coordinates, V planes, U rows) and
+    the near field's 2 conversions (coordinates, V^T); then either test matrices + sketch +
+    combine (3; mixed 5 with staged coordinates and X planes) or the tagged sketch (FP64: gather
+    + sketch; mixed: staged coordinates, [G|H] planes, tau, sketch)."""
+    base = 4 + 2 + (1 if selfadjoint else 2) + 1 + 2 + 1 + (4 + 2 if mixed else 0)
+    return base + ((4 if mixed else 2) if tagged else (5 if mixed else 3))
+
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -244,14 +255,8 @@ class Runner:
         self.mmax_dev = torch.empty(1, dtype=torch.int32, device=dev)
         self.host_total = torch.empty(1, dtype=torch.int64).pin_memory()
         self.host_mmax = torch.empty(1, dtype=torch.int32).pin_memory()
-        # tessellate 4, offsets 2, col 2, coupling 1, near field 2 (+1 split in mixed), decode 1,
-        # and either test matrices + sketch + combine (3; +2 splits in mixed) or the tagged
-        # sketch (1 FP64 gather + 1, or 3 splits + 1 in mixed)
-        mixed = w.get("precision", 0) == 1
-        base = 4 + 2 + 2 + 1 + 2 + 1 + (1 if mixed else 0)
-        base += (2 if self.selfadjoint else 3) if mixed else 0   # coupling operand conversions
-        self.launches_per_step = base + ((4 if mixed else 2) if self.tagged else
-                                         (5 if mixed else 3)) - (1 if self.selfadjoint else 0)
+        self.launches_per_step = launches_per_compression(
+            w.get("precision", 0) == 1, self.tagged, self.selfadjoint)
 
     def step(self, ev=None):
         tb, L, P, o = self.tb, self.tb.lib(), self.tb.ctypes.byref(self.prob), self.out
@@ -608,7 +613,7 @@ def run_batch(args):
                        "precision": args.precision, "sketch": args.sketch,
                        "execution": "one CUDA graph per step, 8 worker streams",
                        "l2": "per-step working set tens of GB, far above L2"},
-            "gpu_launches": sum(1 for _ in jobs) * 15 * args.steps,
+            "gpu_launches": len(jobs) * launches_per_compression(prec == 1, sk == 1) * args.steps,
             "clocks": sampler.summary(), "cpu_baseline": None}
 
 
@@ -671,6 +676,7 @@ def run_serve(args):
                        "server": "8 stream slots, budget 60% of free HBM, host buffers pinned"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "server_stats": {k: stats[k] for k in ("completed", "failed", "mem_peak", "throughput")},
+            "gpu_launches": args.requests * launches_per_compression(prec == 1, sk == 1),
             "cpu_baseline": None}
 
 
