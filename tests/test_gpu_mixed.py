@@ -194,3 +194,49 @@ def test_mixed_coupling_matches_dense_definition(kind, d, grid, n, k, hi, selfad
     err = metrics.rel(at, ref)
     print(f"mixed coupling {kind} n={n} k={k} selfadjoint={selfadjoint}: rel err {err:.3e}")
     assert err < MIXED_BOUND / 4
+
+
+def test_simt_coupling_form_matches_dense_definition(tmp_path):
+    """TBLR_COUPLING_SIMT=1 (read once per process, so run in a child) selects the FP32 SIMT form
+    of the mixed coupling; both forms must meet the same bound against U_i^T A_ij V_j (§2.5)."""
+    import os
+    import subprocess
+    import sys
+    out = tmp_path / "at.npy"
+    code = f"""
+import numpy as np, torch
+from oracle import tagging as orc
+from paper_2501_05528_gb300 import inputs, tblr as tb
+n, d, grid, k = 2100, 3, (2, 2, 2), 20
+pts = inputs.uniform_points(n, d, seed=5)
+tess = orc.tessellate(pts, grid, (0.,) * d, (1.,) * d)
+rng = np.random.default_rng(6)
+U, V = rng.standard_normal((n, k)) / 16, rng.standard_normal((n, k)) / 16
+ranks = np.minimum(k, np.diff(tess["offsets"])).astype(np.int32)
+prob = tb.make_problem(d, "laplace3d", n, grid, (0.,) * d, (1.,) * d, k, 10, 3,
+                       precision=tb.MIXED, sketch=tb.SKETCH_TAGGED)
+t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+lay = tb.tblr_tessellate(prob, t(pts))
+at = tb.tblr_coupling(prob, lay, t(U), t(V), t(ranks), int(np.diff(tess["offsets"]).max()))
+assert tb.tblr_device_timeouts() == 0
+np.save({str(out)!r}, at.cpu().numpy())
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, TBLR_COUPLING_SIMT="1", PYTHONPATH=root)
+    subprocess.run([sys.executable, "-c", code], check=True, cwd=root, env=env, timeout=600)
+    at_simt = np.load(out)
+    n, d, grid, k = 2100, 3, (2, 2, 2), 20
+    pts = inputs.uniform_points(n, d, seed=5)
+    tess = orc.tessellate(pts, grid, (0.0,) * d, (1.0,) * d)
+    perm, off = tess["perm"], tess["offsets"]
+    rng = np.random.default_rng(6)
+    U, V = rng.standard_normal((n, k)) / 16, rng.standard_normal((n, k)) / 16
+    A = orc.dense_matrix(orc.KernelOperator("laplace3d", pts[perm]))
+    b = len(off) - 1
+    ref = np.zeros((b, b, k, k))
+    for i in range(b):
+        for j in range(b):
+            ref[i, j] = U[off[i]:off[i + 1]].T @ A[off[i]:off[i + 1], off[j]:off[j + 1]] @ V[off[j]:off[j + 1]]
+    err = metrics.rel(at_simt, ref)
+    print(f"SIMT coupling form: rel err {err:.3e}")
+    assert err < MIXED_BOUND / 4
