@@ -587,6 +587,18 @@ def run_batch(args):
         t = lambda a: torch.as_tensor(a, device=dev)
         jobs.append(tb.BatchJob(spec_problem(tb, s, prec, sk), t(pts), t(T), t(G), t(H)))
     tb.tblr_batch_plan(jobs)
+    # Autotuner: the tensor-core sketch's tile width, once per size class (kernel, sketch
+    # columns, floor(log2 N)), timed on the class's first job before the graph is captured.
+    tuned = {}
+    if prec == 1 and sk == 1:
+        for job in jobs:
+            if tb.tblr_tuned_width(job.prob):
+                continue
+            _, tau, _ = tb.tblr_decode(job.prob, job.lay, job.T)
+            w, _, _ = tb.tblr_tune_tagged_sketch(job.prob, job.lay, tau, job.G, job.H)
+            tuned[f"kernel{job.prob.kernel}_cols{2 * (job.prob.k + job.prob.p)}_log2n"
+                  f"{job.prob.n.bit_length() - 1}"] = w
+        torch.cuda.synchronize()
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         graph = tb.Graph(jobs, n_streams=8)
@@ -612,6 +624,7 @@ def run_batch(args):
                        "N": "U{4096..65536}", "box": "{128,256,512}", "k": "{16,32,64}",
                        "precision": args.precision, "sketch": args.sketch,
                        "execution": "one CUDA graph per step, 8 worker streams",
+                       "autotuned_tile_widths": tuned,
                        "l2": "per-step working set tens of GB, far above L2"},
             "gpu_launches": len(jobs) * launches_per_compression(prec == 1, sk == 1) * args.steps,
             "clocks": sampler.summary(), "cpu_baseline": None}

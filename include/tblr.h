@@ -221,6 +221,24 @@ int tblr_tagged_sketch(const tblr_problem *prob, const tblr_layout *lay, const d
                        const double *tau, const double *G, const double *H, double *s,
                        double *rr, void *ws, size_t ws_bytes, void *stream);
 
+/* Tile-width autotuner of the mixed-precision tag-factored sketch (TBLR_MIXED
+ * with a built-in kernel).  Runs tblr_tagged_sketch with each admissible
+ * tensor-core tile width (32, 64, 96, 128, 160 columns, at most 64 padded
+ * columns beyond the 32-column round-up of the sketch columns), timing two
+ * runs after a warm-up with CUDA events on `stream` (so it synchronises the
+ * stream and must not be captured in a graph), and records the fastest width
+ * for this process under (kernel, sketch columns, floor(log2 n)); later
+ * tagged sketches of that class use it, including ones captured into graphs.
+ * Arguments as tblr_tagged_sketch; *width (host) receives the chosen width and
+ * s (and rr) hold that width's result.  tblr_tuned_width gives the width the
+ * class currently uses (0: the built-in rule: fewest tiles of at most 160
+ * columns); tblr_tune_clear forgets every recorded width. */
+int tblr_tune_tagged_sketch(const tblr_problem *prob, const tblr_layout *lay, const double *tau,
+                            const double *G, const double *H, double *s, double *rr, void *ws,
+                            size_t ws_bytes, int32_t *width /* host */, void *stream);
+int tblr_tuned_width(const tblr_problem *prob, int32_t *width /* host */);
+void tblr_tune_clear(void);
+
 /* ------------------------------------ a4: tag decode (§4.1, §5.1, §5.3)
  * z_i = unit vector of null(T(N_i, :)) nearest to 1/sqrt(ell) (the normalised
  * projection of the all-ones direction; eq. tagsubmat), tau_i = T z_i (projected

@@ -34,6 +34,9 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "coupling_tc.cuh"
 #include "kernels_f32.cuh"
@@ -517,6 +520,44 @@ ColTiles col_tiles(int64_t ncols, bool tagged) {
   return t;
 }
 
+// Tile widths of the tag-factored sketch and the ones a tuner may try for
+// `ncols` columns: at most 64 padded columns beyond the 32-column round-up.
+constexpr int kTagWidths[5] = {32, 64, 96, 128, 160};
+bool tagged_width_ok(int64_t ncols, int w) {
+  return cdiv(std::max<int64_t>(ncols, 1), w) * w <= cdiv(std::max<int64_t>(ncols, 1), 32) * 32 + 64;
+}
+int64_t tagged_padded_max(int64_t ncols) {
+  int64_t mx = col_tiles(ncols, true).padded;
+  for (int w : kTagWidths)
+    if (tagged_width_ok(ncols, w)) mx = std::max<int64_t>(mx, cdiv(std::max<int64_t>(ncols, 1), w) * w);
+  return mx;
+}
+ColTiles col_tiles_w(int64_t ncols, int w) {
+  ColTiles t;
+  t.width = w;
+  t.ntiles = (int)cdiv(std::max<int64_t>(ncols, 1), w);
+  t.padded = (int64_t)w * t.ntiles;
+  return t;
+}
+
+// Tile widths picked by tblr_tune_tagged_sketch, per (kernel, columns, size
+// class floor(log2 n)), for this process; a width forced by the tuner while it
+// times the candidates (this thread only).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int>, int> g_tune;
+thread_local int t_force_width = 0;
+int size_class(int64_t n) {
+  int c = 0;
+  while (c < 62 && ((int64_t)1 << (c + 1)) <= n) ++c;
+  return c;
+}
+int chosen_width(const Prob &P, int64_t ncols) {
+  if (t_force_width) return t_force_width;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  const auto it = g_tune.find(std::make_tuple(P.kernel, ncols, size_class(P.n)));
+  return it == g_tune.end() ? 0 : it->second;
+}
+
 struct MixedLayout {
   int64_t npad, ncols_pad;
   size_t head, coords, planes, tau, boxes, total;
@@ -525,7 +566,7 @@ struct MixedLayout {
 MixedLayout mixed_layout(const Prob &P, int64_t ncols, bool tagged) {
   MixedLayout L;
   L.npad = cdiv(P.n, KC) * KC;
-  L.ncols_pad = col_tiles(ncols, tagged).padded;
+  L.ncols_pad = tagged ? tagged_padded_max(ncols) : col_tiles(ncols, false).padded;
   L.head = 256;
   L.coords = align256(sizeof(float) * 2 * 3 * L.npad);
   L.planes = align256(sizeof(__nv_bfloat16) * L.npad * L.ncols_pad);
@@ -702,7 +743,8 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
   tau_to_f32<<<(unsigned)std::min<int64_t>(cdiv(P.b * P.b, 256), 1024), 256, 0, s>>>(tau, P.b * P.b,
                                                                                      tf);
   TBLR_TRY(launch_status("tau_to_f32"));
-  const ColTiles ct = col_tiles(ncols, true);
+  const int tw = chosen_width(P, ncols);
+  const ColTiles ct = tw ? col_tiles_w(ncols, tw) : col_tiles(ncols, true);
   Maps maps;
   TBLR_TRY(make_maps(&maps, pl, L, ct.width));
   MixedArgs a = base_args(P, L, qst, boxpad, status);
@@ -719,6 +761,84 @@ int tagged_sketch_mixed(const Prob &P, const tblr_layout *lay, const double *tau
 }
 
 }  // namespace tblr
+
+namespace {
+// Resets the forced width however the tuner leaves its loop.
+struct ForceWidth {
+  explicit ForceWidth(int w) { tblr::t_force_width = w; }
+  ~ForceWidth() { tblr::t_force_width = 0; }
+};
+}  // namespace
+
+extern "C" int tblr_tune_tagged_sketch(const tblr_problem *prob, const tblr_layout *lay,
+                                       const double *tau, const double *G, const double *H,
+                                       double *s_out, double *r_out, void *ws, size_t ws_bytes,
+                                       int32_t *width, void *stream) {
+  using namespace tblr;
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_TRY(check_layout(P, lay));
+  TBLR_REQUIRE(P.precision == TBLR_MIXED &&
+                   (P.kernel == TBLR_KERNEL_LAPLACE2D || P.kernel == TBLR_KERNEL_LAPLACE3D),
+               "tuning applies to the mixed-precision sketch of the built-in kernels");
+  TBLR_REQUIRE(tau && G && s_out && width && (P.selfadjoint || (H && r_out)),
+               "tau, G, s, width (and, unless self-adjoint, H and rr) must be non-NULL");
+  TBLR_REQUIRE(ws != nullptr && ws_bytes >= tagged_mixed_workspace(P),
+               "tagged sketch workspace too small");
+  cudaStream_t s = as_stream(stream);
+  const int64_t ncols = (P.selfadjoint ? 1 : 2) * P.r;
+  cudaEvent_t e0, e1;
+  TBLR_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    set_error("cudaEventCreate failed");
+    return TBLR_ECUDA;
+  }
+  int best = 0, st = TBLR_OK;
+  float best_ms = 0.f;
+  for (int w : kTagWidths) {
+    if (!tagged_width_ok(ncols, w)) continue;
+    ForceWidth force(w);
+    st = tagged_sketch_mixed(P, lay, tau, G, H, s_out, r_out, ws, ws_bytes, s);  // warm-up
+    if (st == TBLR_OK && cudaEventRecord(e0, s) != cudaSuccess) st = TBLR_ECUDA;
+    for (int rep = 0; rep < 2 && st == TBLR_OK; ++rep)
+      st = tagged_sketch_mixed(P, lay, tau, G, H, s_out, r_out, ws, ws_bytes, s);
+    float ms = 0.f;
+    if (st == TBLR_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                          cudaEventSynchronize(e1) != cudaSuccess ||
+                          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = TBLR_ECUDA;
+    if (st != TBLR_OK) break;
+    if (best == 0 || ms < best_ms) {
+      best = w;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != TBLR_OK) return st;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[std::make_tuple(P.kernel, ncols, size_class(P.n))] = best;
+  }
+  *width = best;
+  // Leave the chosen width's result in s (and rr).
+  return tagged_sketch_mixed(P, lay, tau, G, H, s_out, r_out, ws, ws_bytes, s);
+}
+
+extern "C" int tblr_tuned_width(const tblr_problem *prob, int32_t *width) {
+  using namespace tblr;
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_REQUIRE(width != nullptr, "width is NULL");
+  *width = chosen_width(P, (P.selfadjoint ? 1 : 2) * P.r);
+  return TBLR_OK;
+}
+
+extern "C" void tblr_tune_clear(void) {
+  std::lock_guard<std::mutex> g(tblr::g_tune_mu);
+  tblr::g_tune.clear();
+}
 
 extern "C" int tblr_device_timeouts(unsigned int *count) {
   TBLR_REQUIRE(count != nullptr, "count is NULL");

@@ -93,6 +93,10 @@ _SIGNATURES = {
     "tblr_decode": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP]),
     "tblr_tagged_sketch_workspace": (_SZ, [_PP]),
     "tblr_tagged_sketch": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "tblr_tune_tagged_sketch": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP, _VP, _SZ,
+                                               ctypes.POINTER(ctypes.c_int32), _VP]),
+    "tblr_tuned_width": (ctypes.c_int, [_PP, ctypes.POINTER(ctypes.c_int32)]),
+    "tblr_tune_clear": (None, []),
     "tblr_combine": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP]),
     "tblr_col_workspace": (_SZ, [_PP]),
     "tblr_col": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _SZ, _VP]),
@@ -289,6 +293,31 @@ def tblr_tagged_sketch(prob, lay, tau, G, H, dense=None):
     _check(lib().tblr_tagged_sketch(ctypes.byref(prob), lay.ref, _p(dense), _p(tau), _p(G), _p(H),
                                     _p(s), _p(rr), _p(ws), nbytes, _stream()), "tblr_tagged_sketch")
     return (s, s) if prob.sketch & SKETCH_SELFADJOINT else (s, rr)
+
+
+def tblr_tune_tagged_sketch(prob, lay, tau, G, H):
+    """Time every admissible tile width of the mixed tagged sketch on this problem and record
+    the fastest for its class (this process).  Returns (width, S, R) with the chosen width's S, R."""
+    sz = tblr_sizes_of(prob)
+    s = torch.empty(prob.n, sz.r, dtype=torch.float64, device=_dev())
+    rr = torch.empty_like(s)
+    nbytes = lib().tblr_tagged_sketch_workspace(ctypes.byref(prob))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=_dev())
+    w = ctypes.c_int32(0)
+    _check(lib().tblr_tune_tagged_sketch(ctypes.byref(prob), lay.ref, _p(tau), _p(G), _p(H), _p(s),
+                                         _p(rr), _p(ws), nbytes, ctypes.byref(w), _stream()),
+           "tblr_tune_tagged_sketch")
+    return w.value, s, (s if prob.sketch & SKETCH_SELFADJOINT else rr)
+
+
+def tblr_tuned_width(prob) -> int:
+    w = ctypes.c_int32(0)
+    _check(lib().tblr_tuned_width(ctypes.byref(prob), ctypes.byref(w)), "tblr_tuned_width")
+    return w.value
+
+
+def tblr_tune_clear() -> None:
+    lib().tblr_tune_clear()
 
 
 def tblr_combine(prob, lay, yz, z):

@@ -240,3 +240,37 @@ np.save({str(out)!r}, at.cpu().numpy())
     err = metrics.rel(at_simt, ref)
     print(f"SIMT coupling form: rel err {err:.3e}")
     assert err < MIXED_BOUND / 4
+
+
+def test_tile_width_tuner_records_an_admissible_width():
+    """The tagged sketch's tile-width autotuner: every candidate gives the same samples within the
+    mixed bound, the chosen width is admissible and recorded for the class, and later sketches of
+    the class reproduce the tuner's result bit for bit."""
+    tb = _tb()
+    tb.tblr_tune_clear()
+    n, d, grid, k = 2900, 3, (3, 3, 2), 50      # 2r = 120 sketch columns: all five widths admissible
+    pts = inputs.uniform_points(n, d, seed=4242)
+    lo, hi = (0.0,) * d, (1.0,) * d
+    b = int(np.prod(grid))
+    T, G, H = inputs.tagging_draws(b, orc.tag_columns(d, 3), n, k + 10, seed=4243)
+    tess = orc.tessellate(pts, grid, lo, hi)
+    _, tau, _ = orc.decode(T, tess)
+    prob = tb.make_problem(d, "laplace3d", n, grid, lo, hi, k, 10, 3, precision=tb.MIXED,
+                           sketch=tb.SKETCH_TAGGED)
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    lay = tb.tblr_tessellate(prob, t(pts))
+    try:
+        assert tb.tblr_tuned_width(prob) == 0
+        s0, r0 = (x.cpu().numpy() for x in tb.tblr_tagged_sketch(prob, lay, t(tau), t(G), t(H)))
+        w, s1, r1 = tb.tblr_tune_tagged_sketch(prob, lay, t(tau), t(G), t(H))
+        assert w in (32, 64, 96, 128, 160)
+        assert tb.tblr_tuned_width(prob) == w
+        s2, r2 = (x.cpu().numpy() for x in tb.tblr_tagged_sketch(prob, lay, t(tau), t(G), t(H)))
+        assert tb.tblr_device_timeouts() == 0
+        s1, r1 = s1.cpu().numpy(), r1.cpu().numpy()
+        assert np.array_equal(s1, s2) and np.array_equal(r1, r2)
+        assert metrics.rel(s1, s0) < MIXED_BOUND / 4 and metrics.rel(r1, r0) < MIXED_BOUND / 4
+    finally:
+        tb.tblr_tune_clear()
+    assert tb.tblr_tuned_width(prob) == 0
