@@ -80,7 +80,7 @@ struct __align__(1024) CplSmem {
   uint8_t x[STAGES][kParts][KP * 128];    // V_j h, m, l: KP rows x 128 bytes
   float4 qc[kCS][3][4][8];                // chunk coordinates (the mixed apply's layout)
   float w[MB][RS];                        // W of the finished row tile
-  float u[MB][KP];                        // U_i rows of the tile (bulk-copied a tile ahead)
+  float u[MB][KP];                        // U_i rows of the tile (one bulk copy)
   uint64_t cfull[kCS], cfree[kCS];
   uint64_t full_a[STAGES], full_b[STAGES], empty[STAGES];
   uint64_t dfull[2], dempty[2], done, ufull;
