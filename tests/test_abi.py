@@ -69,3 +69,25 @@ def test_null_arguments_are_rejected_before_any_launch(tb):
     assert st == tb.TBLR_EINVAL
     st = tb.lib().tblr_decode(ctypes.byref(prob), None, None, None, None, None, None)
     assert st == tb.TBLR_EINVAL
+
+
+def test_tile_width_tuner_validation_on_host(tb):
+    """The tuner refuses non-mixed problems and missing arguments before any launch; the
+    per-process width table is host state (empty: width 0, the built-in rule)."""
+    lib = tb.lib()
+    lib.tblr_tune_clear()
+    mixed = tb.make_problem(3, "laplace3d", 2900, (3, 3, 2), (0,) * 3, (1,) * 3, k=50,
+                            precision=tb.MIXED, sketch=tb.SKETCH_TAGGED)
+    w = ctypes.c_int32(-1)
+    assert lib.tblr_tuned_width(ctypes.byref(mixed), ctypes.byref(w)) == tb.TBLR_OK
+    assert w.value == 0
+    assert lib.tblr_tuned_width(ctypes.byref(mixed), None) == tb.TBLR_EINVAL
+    empty = tb.LayoutStruct()
+    st = lib.tblr_tune_tagged_sketch(ctypes.byref(mixed), ctypes.byref(empty), None, None, None,
+                                     None, None, None, 0, ctypes.byref(w), None)
+    assert st == tb.TBLR_EINVAL
+    fp64 = tb.make_problem(3, "laplace3d", 2900, (3, 3, 2), (0,) * 3, (1,) * 3, k=50,
+                           sketch=tb.SKETCH_TAGGED)
+    st = lib.tblr_tune_tagged_sketch(ctypes.byref(fp64), ctypes.byref(empty), None, None, None,
+                                     None, None, None, 0, ctypes.byref(w), None)
+    assert st == tb.TBLR_EINVAL
