@@ -254,6 +254,16 @@ int tblr_decode(const tblr_problem *prob, const tblr_layout *lay, const double *
  * (synchronises the device, then resets the count). */
 int tblr_decode_lp_failures(unsigned int *count /* host */);
 
+/* Algorithm 3 (the plain per-box randomized range finder, §4.2 "basic") on the
+ * same machinery: tau[i*b + c] = 0 for c in N_i and 1 otherwise (b x b FP64).
+ * tblr_tagged_sketch with this tau gives S(I_i, :) = A(I_i, F_i) G(F_i) and
+ * R(I_i, :) = A(F_i, I_i)^T H(F_i), Algorithm 3's samples with one shared
+ * Gaussian G (H) restricted to each far field, and tblr_col turns them into
+ * its bases.  With kernel operators this costs the tag-factored sketch's
+ * N^2 2r multiply-adds; as black-box matvecs Algorithm 3 needs 2 b r. */
+int tblr_far_indicator(const tblr_problem *prob, const tblr_layout *lay, double *tau,
+                       void *stream);
+
 /* ------------------------------ a5: combine (Algorithm 2; eq. projected_tags)
  * S(I_i, :) = sum_j z_ij Y(I_i, j r : (j+1) r), R likewise from Z.
  * yz: [n*2C]; s, rr: [n*r]. */

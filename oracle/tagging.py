@@ -502,16 +502,21 @@ def power_method_relerr(apply_diff, apply_diff_t, apply_a, apply_a_t, n, x0, ite
 
 # ---------------------------------------------- Algorithm 3 (cross-check only)
 
-def basic_bases(op, tess, k, r, rng):
-    """Algorithm 3: per box, a Gaussian test matrix zeroed on N_i, then col (2 b r matvecs)."""
+def basic_bases(op, tess, k, r, rng, shared=None):
+    """Algorithm 3: per box, a Gaussian test matrix zeroed on N_i, then col (2 b r matvecs).
+    shared = (G, H), n x r in box-major order: every box uses G and H (zeroed on its N_i)
+    instead of fresh draws from rng."""
     off = tess["offsets"]
     n = op.n
     U = np.zeros((n, k))
     V = np.zeros((n, k))
     ks = box_ranks(tess, k)
     for i in range(tess["b"]):
-        Om = rng.standard_normal((n, r))
-        Ps = rng.standard_normal((n, r))
+        if shared is None:
+            Om = rng.standard_normal((n, r))
+            Ps = rng.standard_normal((n, r))
+        else:
+            Om, Ps = shared[0].copy(), shared[1].copy()
         for j in tess["nbrs"][i]:
             Om[off[j]:off[j + 1]] = 0.0
             Ps[off[j]:off[j + 1]] = 0.0

@@ -742,6 +742,32 @@ extern "C" int tblr_decode(const tblr_problem *prob, const tblr_layout *lay, con
   return launch_status("minratio_kernel");
 }
 
+namespace tblr {
+// tau[i*b + c] = 0 for c in N_i, 1 otherwise (Algorithm 3's far-field mask).
+__global__ void far_indicator_kernel(const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnbr,
+                                     int b, int s3, double *__restrict__ tau) {
+  const int64_t total = (int64_t)b * b;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / b), c = (int)(t % b);
+    bool near = false;
+    for (int s = 0; s < nnbr[i]; ++s) near = near || nbr[(int64_t)i * s3 + s] == c;
+    tau[t] = near ? 0.0 : 1.0;
+  }
+}
+}  // namespace tblr
+
+extern "C" int tblr_far_indicator(const tblr_problem *prob, const tblr_layout *lay, double *tau,
+                                  void *stream) {
+  Prob P;
+  TBLR_TRY(check_problem(prob, &P));
+  TBLR_TRY(check_layout(P, lay));
+  TBLR_REQUIRE(tau != nullptr, "tau must be non-NULL");
+  far_indicator_kernel<<<(unsigned)std::min<int64_t>(cdiv(P.b * P.b, 256), 4096), 256, 0,
+                         as_stream(stream)>>>(lay->nbr, lay->nnbr, (int)P.b, P.s3, tau);
+  return launch_status("far_indicator_kernel");
+}
+
 extern "C" int tblr_decode_lp_failures(unsigned int *count) {
   TBLR_REQUIRE(count != nullptr, "count is NULL");
   unsigned int zero = 0;

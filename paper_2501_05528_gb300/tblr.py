@@ -91,6 +91,7 @@ _SIGNATURES = {
     "tblr_sketch_workspace": (_SZ, [_PP]),
     "tblr_sketch": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "tblr_decode": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP]),
+    "tblr_far_indicator": (ctypes.c_int, [_PP, _PL, _VP, _VP]),
     "tblr_tagged_sketch_workspace": (_SZ, [_PP]),
     "tblr_tagged_sketch": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "tblr_tune_tagged_sketch": (ctypes.c_int, [_PP, _PL, _VP, _VP, _VP, _VP, _VP, _VP, _SZ,
@@ -358,6 +359,15 @@ def tblr_nearfield(prob, lay, u, at, v, ranks, nf_off, m_max: int, total: int, d
                                 _p(ranks), _p(nf_off), m_max, _p(bnear), _p(ws), nbytes, _stream()),
            "tblr_nearfield")
     return bnear
+
+
+def tblr_far_indicator(prob, lay):
+    """Algorithm 3's far-field mask as tags: tau[i, c] = 0 for c in N_i, else 1."""
+    sz = tblr_sizes_of(prob)
+    tau = torch.empty(sz.b, sz.b, dtype=torch.float64, device=_dev())
+    _check(lib().tblr_far_indicator(ctypes.byref(prob), lay.ref, _p(tau), _stream()),
+           "tblr_far_indicator")
+    return tau
 
 
 def tblr_decode_lp_failures() -> int:

@@ -332,3 +332,58 @@ def test_minratio_decode_and_compression_match_oracle(d, grid, n, k, e):
     print(f"minratio d={d} e={e}: mean rho {np.nanmean(rho):.3f} (projected {np.nanmean(rho0):.3f}), "
           f"reconstruction rel err {err:.3e}")
     assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("kind,d,grid,n,k", [("laplace2d", 2, (4, 4), 1500, 6),
+                                            ("laplace3d", 3, (3, 3, 3), 1800, 5)])
+def test_algorithm3_basic_through_the_tagged_sketch(kind, d, grid, n, k):
+    """Algorithm 3 (§4.2, the plain per-box range finder): tags tau_ic = [c not in N_i] make
+    the tag-factored sketch S_i = A(I_i, F_i) G(F_i) (and R_i likewise); S, R, the ranks and the
+    bases must match the oracle's Algorithm 3 run with the same shared G, H."""
+    tb = _tb()
+    p = 10
+    r = k + p
+    lo, hi = (0.0,) * d, (1.0,) * d
+    pts = inputs.uniform_points(n, d, seed=31 + d)
+    b = int(np.prod(grid))
+    T, G, H = inputs.tagging_draws(b, orc.tag_columns(d, 3), n, r, seed=32 + d)
+    tess = orc.tessellate(pts, grid, lo, hi)
+    perm, off = tess["perm"], tess["offsets"]
+    op = orc.KernelOperator(kind, pts[perm])
+    Ub, Vb, ks = orc.basic_bases(op, tess, k, r, None, shared=(G[perm], H[perm]))
+    prob = tb.make_problem(d, kind, n, grid, lo, hi, k, p, 3, sketch=tb.SKETCH_TAGGED)
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    lay = tb.tblr_tessellate(prob, t(pts))
+    tau = tb.tblr_far_indicator(prob, lay).cpu().numpy()
+    tau_ref = np.ones((b, b))
+    for i in range(b):
+        tau_ref[i, tess["nbrs"][i]] = 0.0
+    assert np.array_equal(tau, tau_ref)
+    s, rr = tb.tblr_tagged_sketch(prob, lay, t(tau), t(G), t(H))
+    s_h, r_h = s.cpu().numpy(), rr.cpu().numpy()
+    for i in range(b):
+        rows = slice(off[i], off[i + 1])
+        if off[i + 1] == off[i]:
+            continue
+        Om, Ps = G[perm].copy(), H[perm].copy()
+        for j in tess["nbrs"][i]:
+            Om[off[j]:off[j + 1]] = 0.0
+            Ps[off[j]:off[j + 1]] = 0.0
+        Y = op.apply(Om)[rows]
+        Z = op.apply(Ps, adjoint=True)[rows]
+        if np.linalg.norm(Y) > 0:
+            assert metrics.rel(s_h[rows], Y) < 1e-11
+            assert metrics.rel(r_h[rows], Z) < 1e-11
+    u, ranks = tb.tblr_col(prob, lay, s)
+    v, _ = tb.tblr_col(prob, lay, rr)
+    assert np.array_equal(ranks.cpu().numpy(), ks)
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    for i in range(b):
+        if ks[i] == 0:
+            continue
+        rows = slice(off[i], off[i + 1])
+        for got, ref in ((u, Ub), (v, Vb)):
+            P1 = got[rows, :ks[i]] @ got[rows, :ks[i]].T
+            P2 = ref[rows, :ks[i]] @ ref[rows, :ks[i]].T
+            assert np.abs(P1 - P2).max() < 1e-9
